@@ -1,0 +1,475 @@
+/*
+ * fps_oracle.c -- plain, slow, CPU reference ("oracle") for the spectral Poisson
+ * ADI solver of Fortunato & Townsend, "Fast Poisson solvers for spectral methods"
+ * (arXiv 1710.11259).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent checker of the GPU
+ * library: only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or helper with the
+ * CUDA path, and the CUDA path never calls it.
+ *
+ * Everything is written for clarity: arithmetic in `real` (double, or long double
+ * in the rounding-check build), textbook Thomas elimination with divisions, the
+ * ADI steps in the order of Algorithm 2.  OpenMP only distributes independent
+ * right-hand sides of one banded solve over threads; it does not change the
+ * arithmetic of any single system.
+ *
+ * Readings of the paper taken here (each is argued in the design notes):
+ *   R1  Algorithm 2's first half-step is used in the sign-consistent form
+ *       X_{j+1/2}(B - p_j I) = (A - p_j I) X_j - F; as printed it produces the
+ *       negated half-iterate (the whole iterates are the same either way).
+ *   R2  The symmetrised unknown of (3.9) is recovered by X = D_s Y D_s with
+ *       D_s = |D|^{-1/2}; that is the reading consistent with the printed
+ *       right-hand side D_s^{-1}(D^{-1} F D^{-1})D_s^{-1}.
+ *   R3  The number of iterations is (2.9), J = ceil(log(16 gamma) log(4/eps)/pi^2),
+ *       with the cross-ratio gamma of the intervals (as in Appendix A); the
+ *       simplified count printed for the square in Sec. 3.3 is not used.
+ *   R4  The spectral intervals are those of Lemma B.2: sigma(A~) in
+ *       [-1, -1/(30 n^4)], sigma(B~) = -sigma(A~).
+ */
+#include <stdlib.h>
+#include <string.h>
+#include <tgmath.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
+
+static const real ORC_PI = (real)3.14159265358979323846264338327950288L;
+
+/* ------------------------------------------------------------------------- */
+/* Section 3.2, eq. (3.7): multiplication by (1 - x^2) in the normalised       */
+/* ultraspherical basis C~^(3/2), and D_jj = -(j(j+3)+2).                      */
+/* ------------------------------------------------------------------------- */
+
+/* M_{j,j} = 2(j+1)(j+2) / ((2j+1)(2j+5)) */
+static real M_diag(long j)
+{
+    real J = (real)j;
+    return 2 * (J + 1) * (J + 2) / ((2 * J + 1) * (2 * J + 5));
+}
+
+/* M_{j,j+2} = -1/((2j+3)(2j+5)) * sqrt( (j+4)!/j! * (2j+3)/(2j+7) ),
+ * with (j+4)!/j! = (j+1)(j+2)(j+3)(j+4).  M_{j,j+1} = 0. */
+static real M_off2(long j)
+{
+    real J = (real)j;
+    real fact_ratio = (J + 1) * (J + 2) * (J + 3) * (J + 4);
+    return -sqrt(fact_ratio * (2 * J + 3) / (2 * J + 7)) / ((2 * J + 3) * (2 * J + 5));
+}
+
+/* D_{j,j} = -(j(j+3)+2), eq. (3.6) */
+static real D_diag(long j)
+{
+    real J = (real)j;
+    return -(J * (J + 3) + 2);
+}
+
+/* Exported for the quadrature pin: the first n diagonal entries of M and the
+ * n-2 entries M_{j,j+2}. */
+void orc_M_bands(long n, double *diag, double *off2)
+{
+    for (long j = 0; j < n; ++j) diag[j] = (double)M_diag(j);
+    for (long j = 0; j + 2 < n; ++j) off2[j] = (double)M_off2(j);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Section 3.3, eq. (3.8)-(3.9): A = D^{-1} M, A~ = D_s^{-1} A D_s symmetric.   */
+/* A~ is pentadiagonal with zero first off-diagonals, i.e. a "stride-2"        */
+/* symmetric tridiagonal: diagonal ad[j], coupling ae[j] between j and j+2.    */
+/* ------------------------------------------------------------------------- */
+
+/* D_s such that D_s^{-1} A D_s is symmetric: (D_s)_jj = |D_jj|^{-1/2}. */
+static real Ds_diag(long j) { return 1 / sqrt(-D_diag(j)); }
+
+static void square_bands(long n, real *ad, real *ae)
+{
+    for (long j = 0; j < n; ++j) {
+        real A_jj = M_diag(j) / D_diag(j);                 /* (D^{-1} M)_{jj} */
+        ad[j] = A_jj;                                       /* similarity keeps the diagonal */
+    }
+    for (long j = 0; j + 2 < n; ++j) {
+        real A_j_j2 = M_off2(j) / D_diag(j);               /* (D^{-1} M)_{j,j+2} */
+        ae[j] = A_j_j2 * Ds_diag(j + 2) / Ds_diag(j);       /* (D_s^{-1} A D_s)_{j,j+2} */
+    }
+}
+
+void orc_square_bands(long n, double *ad, double *ae)
+{
+    real *d = malloc(sizeof(real) * (size_t)n), *e = malloc(sizeof(real) * (size_t)(n > 2 ? n : 1));
+    square_bands(n, d, e);
+    for (long j = 0; j < n; ++j) ad[j] = (double)d[j];
+    for (long j = 0; j + 2 < n; ++j) ae[j] = (double)e[j];
+    free(d);
+    free(e);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Elliptic functions for Theorem 2.1 / Appendix A.                            */
+/* Parameter convention: m = kappa^2 (MATLAB's ellipke/ellipj convention).      */
+/* ------------------------------------------------------------------------- */
+
+/* Complete elliptic integral of the first kind via the arithmetic-geometric
+ * mean, K(m) = pi / (2 AGM(1, sqrt(1-m)))  (DLMF 19.8.5). */
+static real ellip_K(real m)
+{
+    real a = 1, b = sqrt(1 - m);
+    for (int it = 0; it < 64 && fabs(a - b) > 4 * (real)1e-19 * a; ++it) {
+        real an = (a + b) / 2;
+        b = sqrt(a * b);
+        a = an;
+    }
+    return ORC_PI / (2 * a);
+}
+
+/* Jacobi dn(u | m) by the descending Landen / AGM scheme (DLMF 22.20(ii)):
+ * a_0 = 1, b_0 = sqrt(1-m), c_0 = sqrt(m); a_{k+1} = (a_k+b_k)/2,
+ * b_{k+1} = sqrt(a_k b_k), c_{k+1} = (a_k-b_k)/2 until c_N ~ 0;
+ * phi_N = 2^N a_N u, phi_{k-1} = (phi_k + asin(c_k sin(phi_k)/a_k))/2;
+ * dn = cos(phi_0)/cos(phi_1 - phi_0). */
+static real ellip_dn(real u, real m)
+{
+    real a[80], c[80];
+    real b = sqrt(1 - m);
+    a[0] = 1;
+    c[0] = sqrt(m);
+    int N = 0;
+    while (N < 70 && fabs(c[N]) > (real)1e-18) {
+        a[N + 1] = (a[N] + b) / 2;
+        c[N + 1] = (a[N] - b) / 2;
+        b = sqrt(a[N] * b);
+        ++N;
+    }
+    if (N == 0) return 1; /* m == 0: dn == 1 */
+    real phi = ldexp(a[N] * u, N);
+    real phi_prev = phi;
+    for (int k = N; k >= 1; --k) {
+        phi_prev = phi;
+        phi = (phi + asin(c[k] * sin(phi) / a[k])) / 2;
+    }
+    /* phi now holds phi_0 and phi_prev holds phi_1 */
+    return cos(phi) / cos(phi_prev - phi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. (2.9) and Appendix A: iteration count and Zolotarev shifts for          */
+/* A X - X B = F with sigma(A) in [a,b], sigma(B) in [c,d], a < b < c < d.     */
+/* ------------------------------------------------------------------------- */
+
+/* gamma = |c-a||d-b| / (|c-b||d-a|)  (Theorem 2.1) */
+static real cross_ratio(real a, real b, real c, real d)
+{
+    return fabs(c - a) * fabs(d - b) / (fabs(c - b) * fabs(d - a));
+}
+
+/* J = ceil( log(16 gamma) log(4/eps) / pi^2 )  (2.9) */
+int orc_adi_iterations(double a, double b, double c, double d, double tol)
+{
+    real gam = cross_ratio(a, b, c, d);
+    real J = ceil(log(16 * gam) * log(4 / (real)tol) / (ORC_PI * ORC_PI));
+    return (int)J;
+}
+
+/* Shifts (2.4): p_j = T(-alpha dn[(2j+1)K/(2J), kappa]), q_j = T(+alpha dn[...]),
+ * kappa = sqrt(1 - 1/alpha^2), alpha = -1 + 2 gamma + 2 sqrt(gamma^2 - gamma),
+ * T the Moebius map taking (-alpha, -1, 1, alpha) to (a, b, c, d).
+ * Writes J values into p and q; returns J. */
+int orc_adi_shifts(double a_, double b_, double c_, double d_, double tol, int J, double *p, double *q)
+{
+    real a = a_, b = b_, c = c_, d = d_;
+    real gam = cross_ratio(a, b, c, d);
+    real alp = -1 + 2 * gam + 2 * sqrt(gam * gam - gam);
+
+    /* Moebius T(z) = (TA z + TB)/(TC z + TD) with T(1)=c, T(-1)=b, T(-alp)=a.
+     * From T(1)=c and T(-1)=b: 2 TA = (c+b) TC + (c-b) TD, 2 TB = (c-b) TC + (c+b) TD;
+     * T(-alp)=a then fixes TC : TD up to scale. */
+    real TC = (c + b) - alp * (c - b) - 2 * a;
+    real TD = alp * (c + b) - (c - b) - 2 * a * alp;
+    real TA = ((c + b) * TC + (c - b) * TD) / 2;
+    real TB = ((c - b) * TC + (c + b) * TD) / 2;
+
+    for (int j = 0; j < J; ++j) {
+        real dn;
+        if (alp < (real)1e7) {
+            real m = 1 - 1 / (alp * alp);
+            real K = ellip_K(m);
+            real u = ((real)j + (real)0.5) * K / (real)J;
+            dn = ellip_dn(u, m);
+        } else {
+            /* kappa' = 1/alp is tiny: leading terms of the expansions about m = 1,
+             * K = log(4/kappa') + (kappa'^2/4)(log(4/kappa') - 1)   (DLMF 19.12.1),
+             * dn(u) = sech u + (kappa'^2/4)(sinh u cosh u + u) tanh u sech u (DLMF 22.10.ii). */
+            real m1 = 1 / (alp * alp);
+            real L4 = log(4 * alp);
+            real K = L4 + m1 * (L4 - 1) / 4;
+            real u = ((real)j + (real)0.5) * K / (real)J;
+            real sech = 1 / cosh(u);
+            dn = sech + m1 / 4 * (sinh(u) * cosh(u) + u) * tanh(u) * sech;
+        }
+        real zp = -alp * dn, zq = alp * dn;
+        p[j] = (double)((TA * zp + TB) / (TC * zp + TD));
+        q[j] = (double)((TA * zq + TB) / (TC * zq + TD));
+    }
+    return J;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Banded pieces of Algorithm 2.  A "stride-s tridiagonal" symmetric matrix T  */
+/* has diagonal td[i] and off-diagonal tu[i] = T[i][i+s] = T[i+s][i]; indices  */
+/* of different residue mod s never couple, so a solve splits into s           */
+/* independent tridiagonal systems (App. B, P3).  s = 1 for the finite-        */
+/* difference matrix K of (1.2), s = 2 for A~ of (3.9).                        */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    long n;
+    int s;
+    const real *td, *tu;
+} band_t;
+
+/* Thomas elimination of (T - sigma I): for each index i,
+ *   den[i] = (t_ii - sigma) - sub_i * cp[i-s],   cp[i] = tu[i] / den[i],
+ * with sub_i = tu[i-s] (zero for the first index of each residue class).
+ * The factors depend only on the matrix, so they are shared by every
+ * right-hand side.  (Thomas algorithm, cited by the paper for P3.) */
+static void thomas_factor(const band_t *T, real sigma, real *cp, real *den)
+{
+    long n = T->n;
+    int s = T->s;
+    for (long i = 0; i < n; ++i) {
+        real diag = T->td[i] - sigma;
+        if (i >= s) {
+            real sub = T->tu[i - s];
+            den[i] = diag - sub * cp[i - s];
+        } else {
+            den[i] = diag;
+        }
+        cp[i] = (i + s < n) ? T->tu[i] / den[i] : 0;
+    }
+}
+
+/* X = (T - sigma I)^{-1} R acting on columns (left multiplication).  R and X
+ * are n x ncol row-major; X may alias R.  Forward sweep
+ * dp[i] = (r[i] - sub_i dp[i-s]) / den[i], backward x[i] = dp[i] - cp[i] x[i+s]. */
+static void solve_left(const band_t *T, real sigma, long ncol, const real *R, real *X, real *cp, real *den)
+{
+    long n = T->n;
+    int s = T->s;
+    thomas_factor(T, sigma, cp, den);
+    /* Each thread owns a contiguous range of columns and walks the rows in the
+     * order of the recurrence, so that memory is read row by row. */
+#pragma omp parallel
+    {
+        long c0 = 0, c1 = ncol;
+#ifdef _OPENMP
+        int nt = omp_get_num_threads(), id = omp_get_thread_num();
+        c0 = ncol * id / nt;
+        c1 = ncol * (id + 1) / nt;
+#endif
+        for (long i = 0; i < n; ++i)
+            for (long c = c0; c < c1; ++c) {
+                real r = R[i * ncol + c];
+                if (i >= s) r -= T->tu[i - s] * X[(i - s) * ncol + c];
+                X[i * ncol + c] = r / den[i];
+            }
+        for (long i = n - 1; i >= 0; --i)
+            if (i + s < n)
+                for (long c = c0; c < c1; ++c) X[i * ncol + c] -= cp[i] * X[(i + s) * ncol + c];
+    }
+}
+
+/* X = R (T - sigma I)^{-1} acting on rows (right multiplication; T symmetric so
+ * each row x solves (T - sigma I) x^T = r^T).  R, X are nrow x n row-major. */
+static void solve_right(const band_t *T, real sigma, long nrow, const real *R, real *X, real *cp, real *den)
+{
+    long n = T->n;
+    int s = T->s;
+    thomas_factor(T, sigma, cp, den);
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < nrow; ++r) {
+        const real *rr = R + r * n;
+        real *xr = X + r * n;
+        for (long i = 0; i < n; ++i) {
+            real v = rr[i];
+            if (i >= s) v -= T->tu[i - s] * xr[i - s];
+            xr[i] = v / den[i];
+        }
+        for (long i = n - 1; i >= 0; --i) {
+            if (i + s < n) xr[i] -= cp[i] * xr[i + s];
+        }
+    }
+}
+
+/* Y = (T - sigma I) X  (left multiplication, acts along columns). */
+static void mul_left(const band_t *T, real sigma, long ncol, const real *X, real *Y)
+{
+    long n = T->n;
+    int s = T->s;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i) {
+        for (long c = 0; c < ncol; ++c) {
+            real v = (T->td[i] - sigma) * X[i * ncol + c];
+            if (i >= s) v += T->tu[i - s] * X[(i - s) * ncol + c];
+            if (i + s < n) v += T->tu[i] * X[(i + s) * ncol + c];
+            Y[i * ncol + c] = v;
+        }
+    }
+}
+
+/* Y = X (T - sigma I)  (right multiplication, acts along rows; T symmetric). */
+static void mul_right(const band_t *T, real sigma, long nrow, const real *X, real *Y)
+{
+    long n = T->n;
+    int s = T->s;
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < nrow; ++r) {
+        const real *xr = X + r * n;
+        real *yr = Y + r * n;
+        for (long k = 0; k < n; ++k) {
+            real v = (T->td[k] - sigma) * xr[k];
+            if (k >= s) v += T->tu[k - s] * xr[k - s];
+            if (k + s < n) v += T->tu[k] * xr[k + s];
+            yr[k] = v;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 2: ADI for A X - X B = F (A, B symmetric stride-s tridiagonals,   */
+/* both n x n), J iterations with shifts p_j, q_j, X_0 = 0.  Reading R1:        */
+/*   X_{j+1/2} (B - p_j I) = (A - p_j I) X_j - F                               */
+/*   (A - q_j I) X_{j+1}   = F + X_{j+1/2} (B - q_j I)                          */
+/* ------------------------------------------------------------------------- */
+static void adi_sylvester(const band_t *A, const band_t *B, const real *F, int J, const real *p, const real *q,
+                          real *X)
+{
+    long n = A->n;
+    size_t nn = (size_t)n * (size_t)n;
+    real *Xh = malloc(sizeof(real) * nn);
+    real *W = malloc(sizeof(real) * nn);
+    real *cp = malloc(sizeof(real) * (size_t)n), *den = malloc(sizeof(real) * (size_t)n);
+    memset(X, 0, sizeof(real) * nn);
+    for (int j = 0; j < J; ++j) {
+        /* first half-step: W = (A - p_j I) X_j - F, then X_{j+1/2} = W (B - p_j I)^{-1} */
+        mul_left(A, p[j], n, X, W);
+#pragma omp parallel for schedule(static)
+        for (size_t t = 0; t < nn; ++t) W[t] -= F[t];
+        solve_right(B, p[j], n, W, Xh, cp, den);
+        /* second half-step: W = F + X_{j+1/2} (B - q_j I), then X_{j+1} = (A - q_j I)^{-1} W */
+        mul_right(B, q[j], n, Xh, W);
+#pragma omp parallel for schedule(static)
+        for (size_t t = 0; t < nn; ++t) W[t] += F[t];
+        solve_left(A, q[j], n, W, X, cp, den);
+    }
+    free(Xh);
+    free(W);
+    free(cp);
+    free(den);
+}
+
+/* Exported generic driver (used with the finite-difference matrix K of (1.2)
+ * as a closed-form check of the ADI machinery).  Bands in double; J shifts. */
+void orc_adi_sylvester(long n, int s, const double *Ad, const double *Ae, const double *Bd, const double *Be,
+                       const double *F, int J, const double *p, const double *q, double *X)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    long ne = n > s ? n - s : 1;
+    real *ad = malloc(sizeof(real) * (size_t)n), *ae = malloc(sizeof(real) * (size_t)ne);
+    real *bd = malloc(sizeof(real) * (size_t)n), *be = malloc(sizeof(real) * (size_t)ne);
+    real *pr = malloc(sizeof(real) * (size_t)(J > 0 ? J : 1)), *qr = malloc(sizeof(real) * (size_t)(J > 0 ? J : 1));
+    real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
+    for (long i = 0; i < n; ++i) { ad[i] = Ad[i]; bd[i] = Bd[i]; }
+    for (long i = 0; i + s < n; ++i) { ae[i] = Ae[i]; be[i] = Be[i]; }
+    for (int j = 0; j < J; ++j) { pr[j] = p[j]; qr[j] = q[j]; }
+    for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
+    band_t A = {n, s, ad, ae}, B = {n, s, bd, be};
+    adi_sylvester(&A, &B, Fr, J, pr, qr, Xr);
+    for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
+    free(ad); free(ae); free(bd); free(be); free(pr); free(qr); free(Fr); free(Xr);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Section 3 end to end (Table 3.1, steps 2-3) for  M X D^T + D X M^T = F.     */
+/*   1. A~ = D_s^{-1} D^{-1} M D_s, B~ = -A~                     (3.8)-(3.9)   */
+/*   2. F~ = D_s^{-1} (D^{-1} F D^{-1}) D_s^{-1}                 (3.9)         */
+/*   3. intervals [a,b] = [-1, -1/(30 n^4)], [c,d] = [1/(30 n^4), 1] (Lemma B.2)*/
+/*   4. J from (2.9), shifts from (2.4) / Appendix A                           */
+/*   5. Algorithm 2 on A~ Y - Y B~ = F~                                         */
+/*   6. X = D_s Y D_s                                            (reading R2)  */
+/* F, X: n x n row-major, X_ij pairs C~_i(y) with C~_j(x).  Returns J.         */
+/* ------------------------------------------------------------------------- */
+static int poisson_square(long n, double tol, const real *F, real *X, double *shifts_q_out)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    long ne = n > 2 ? n - 2 : 1;
+    real *ad = malloc(sizeof(real) * (size_t)n), *ae = malloc(sizeof(real) * (size_t)ne);
+    real *bd = malloc(sizeof(real) * (size_t)n), *be = malloc(sizeof(real) * (size_t)ne);
+    square_bands(n, ad, ae);
+    for (long j = 0; j < n; ++j) bd[j] = -ad[j];
+    for (long j = 0; j + 2 < n; ++j) be[j] = -ae[j];
+
+    real *Ft = malloc(sizeof(real) * nn), *Y = malloc(sizeof(real) * nn);
+    for (long i = 0; i < n; ++i)
+        for (long k = 0; k < n; ++k) {
+            real g = F[i * n + k] / (D_diag(i) * D_diag(k)); /* D^{-1} F D^{-1} */
+            Ft[i * n + k] = g / (Ds_diag(i) * Ds_diag(k));    /* D_s^{-1} ( . ) D_s^{-1} */
+        }
+
+    double nd = (double)n;
+    double eps_n = 1.0 / (30.0 * nd * nd * nd * nd);
+    double a = -1.0, b = -eps_n, c = eps_n, d = 1.0;
+    int J = orc_adi_iterations(a, b, c, d, tol);
+    double *p = malloc(sizeof(double) * (size_t)J), *q = malloc(sizeof(double) * (size_t)J);
+    orc_adi_shifts(a, b, c, d, tol, J, p, q);
+    real *pr = malloc(sizeof(real) * (size_t)J), *qr = malloc(sizeof(real) * (size_t)J);
+    for (int j = 0; j < J; ++j) { pr[j] = p[j]; qr[j] = q[j]; }
+    if (shifts_q_out)
+        for (int j = 0; j < J; ++j) shifts_q_out[j] = q[j];
+
+    band_t A = {n, 2, ad, ae}, B = {n, 2, bd, be};
+    adi_sylvester(&A, &B, Ft, J, pr, qr, Y);
+
+    for (long i = 0; i < n; ++i)
+        for (long k = 0; k < n; ++k) X[i * n + k] = Ds_diag(i) * Y[i * n + k] * Ds_diag(k);
+
+    free(ad); free(ae); free(bd); free(be); free(Ft); free(Y); free(p); free(q); free(pr); free(qr);
+    return J;
+}
+
+int orc_poisson_square(long n, double tol, const double *F, double *X)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
+    for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
+    int J = poisson_square(n, tol, Fr, Xr, NULL);
+    for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
+    free(Fr);
+    free(Xr);
+    return J;
+}
+
+/* Threads OpenMP will use (reported beside the CPU-baseline timings). */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* sizeof(real): 8 for the double build, 16 (80-bit payload) for long double. */
+int orc_real_bytes(void) { return (int)sizeof(real); }
