@@ -1,0 +1,176 @@
+/*
+ * fps.h -- C ABI of the GB300 (sm_103a) spectral Poisson solver.
+ *
+ * The library solves the discretisation of Poisson's equation with homogeneous
+ * Dirichlet conditions on [-1,1]^2 (and [-1,1]^3) in the normalised
+ * ultraspherical basis C~^(3/2) of Fortunato & Townsend, "Fast Poisson solvers
+ * for spectral methods" (arXiv 1710.11259):
+ *
+ *     square:  M X D^T + D X M^T = F                         (Sec. 3.2, eq. (3.6))
+ *     cube:    (D_xx + D_yy + D_zz) vec(X) = vec(F)          (Sec. 5, eq. (5.2))
+ *
+ * with M the multiplication-by-(1-x^2) matrix of (3.7) and D = diag(-(j+1)(j+2)).
+ * The solve is the ADI iteration of Algorithm 2 with the Zolotarev shifts of
+ * Theorem 2.1 / eq. (2.4) and the iteration count of eq. (2.9), run on the
+ * symmetrised equation (3.9).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major, FP64, contiguous.  X[i*n + j] pairs C~_i(y) with
+ *     C~_j(x) (expansion (3.2)); F likewise.  Cube tensors are X[(i*n + j)*n + k].
+ *   - Pointers may be device pointers (on the plan's device) or host pointers
+ *     (pageable or pinned).  Device pointers: the call is asynchronous on the
+ *     plan's stream and returns after enqueueing.  Host pointers: the library
+ *     stages through its own device buffers and the call returns after the
+ *     result has been copied back (it synchronises the plan's stream).
+ *   - The caller owns F, X and gradient buffers; the plan owns everything else
+ *     (shift table, per-shift Thomas factors, work arrays, CUDA graph).
+ *   - F is never modified.  X must not overlap F.
+ *   - Errors from argument checks are returned synchronously; errors from the
+ *     device (a failed launch) are returned by the call that detects them.
+ *     fps_last_error() gives a one-line message for the calling thread.
+ *   - A plan is not thread-safe: use one plan per host thread.
+ */
+#ifndef FPS_H
+#define FPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fps_plan fps_plan;
+
+/* Arithmetic of the ADI sweeps. */
+typedef enum {
+    FPS_FP64 = 0,        /* plain method: every sweep in FP64 */
+    FPS_FP32_REFINE = 1  /* FP32 sweeps inside an FP64 iterative refinement of (3.9) */
+} fps_precision;
+
+typedef enum {
+    FPS_OK = 0,
+    FPS_ERR_INVALID_ARG = -1,   /* bad size, tolerance, dimension, pointer */
+    FPS_ERR_UNSUPPORTED = -2,   /* valid request this build does not implement */
+    FPS_ERR_CUDA = -3,          /* a CUDA runtime call or launch failed */
+    FPS_ERR_NOT_CONVERGED = -4, /* refinement missed its target; X holds the best iterate */
+    FPS_ERR_NONFINITE = -5,     /* F (or an intermediate) holds NaN/Inf */
+    FPS_ERR_TIMEOUT = -6        /* a bounded device-side wait gave up */
+} fps_status;
+
+/* Read-only facts about a plan. */
+typedef struct {
+    int64_t n;              /* problem size per dimension (largest n for a batch) */
+    int dim;                /* 2 or 3 */
+    int precision;          /* fps_precision */
+    int nrhs;               /* right-hand sides per problem */
+    int64_t batch;          /* problems in the plan (1 unless batched) */
+    int J;                  /* ADI iterations of the FP64 solve, eq. (2.9) */
+    int J_inner;            /* ADI iterations per refinement round (FP32_REFINE) */
+    int refine_rounds;      /* rounds used by the last FP32_REFINE solve */
+    double last_residual;   /* max |R~| / max |F~| after the last FP32_REFINE solve */
+    double tol;             /* requested tolerance */
+    int64_t device_bytes;   /* device memory owned by the plan */
+} fps_plan_info_t;
+
+/*
+ * fps_plan_create -- plan the solve of one problem of size n (dim = 2: n x n;
+ * dim = 3: n x n x n) for `nrhs` right-hand sides stored back to back.
+ *   tol        relative accuracy eps of Theorem 2.1, 0 < tol < 1 (App. A requires it).
+ *              FP64: the ADI error bound ||Y - Y_J||_2 <= tol ||Y||_2 of (2.9).
+ *              FP32_REFINE: target of max |R~| / max |F~| for the refinement.
+ *   precision  fps_precision.
+ *   stream     cudaStream_t (may be NULL for the legacy default stream); the
+ *              plan's device is the current device at the time of the call.
+ * The plan computes the spectral interval of Lemma B.2, J of (2.9), the shifts
+ * of (2.4) on the host in FP64, uploads them and factors every shifted matrix
+ * A~ - q_j I once (Thomas pivots, App. B even/odd decoupling).
+ * Errors: INVALID_ARG (n < 1, dim not 2/3, tol outside (0,1), nrhs < 1, out NULL),
+ * CUDA (allocation or launch failure).  *out is NULL on error.
+ */
+int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precision, int nrhs, void *stream);
+
+/*
+ * fps_plan_create_batched -- plan `count` independent squares of sizes ns[0..count-1]
+ * (each with its own J and shifts), each with `nrhs` right-hand sides.  Layout
+ * of F and X: problem after problem, each problem's nrhs n_p x n_p matrices back
+ * to back.  Errors as fps_plan_create, plus INVALID_ARG for count < 1 or ns NULL.
+ */
+int fps_plan_create_batched(fps_plan **out, const int64_t *ns, int64_t count, int nrhs, double tol, int precision,
+                            void *stream);
+
+/* Make later calls on this plan enqueue on `stream` (a cudaStream_t). */
+int fps_plan_set_stream(fps_plan *plan, void *stream);
+
+/*
+ * fps_poisson_square_solve -- X = solution of (3.6) for F (per right-hand side,
+ * per problem of a batch).  Algorithm 2 on A~ Y + Y A~ = F~ of (3.9), then
+ * X = D_s Y D_s (the recovery consistent with the printed right-hand side of (3.9)).
+ * Errors: INVALID_ARG (plan NULL or not dim 2, F/X NULL or overlapping),
+ * NONFINITE (FP32_REFINE: F holds NaN/Inf), NOT_CONVERGED (FP32_REFINE missed tol),
+ * CUDA.
+ */
+int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X);
+
+/*
+ * fps_poisson_cube_solve -- X = solution of (5.2) on [-1,1]^3 by the nested ADI of
+ * Sec. 5 (outer split (D_xx + D_yy) | D_zz, middle split D_xx | D_yy, inner
+ * Stein equations per slice).  Errors: INVALID_ARG (plan not dim 3), UNSUPPORTED
+ * when this build has no cube path, CUDA.
+ */
+int fps_poisson_cube_solve(fps_plan *plan, const double *F, double *X);
+
+/*
+ * fps_poisson_adjoint -- dL/dF from dL/dX for the solve of this plan.  The
+ * solve map F -> X is a rational function of the commuting symmetric operators
+ * Y -> A~ Y and Y -> Y A~ wrapped by the diagonal scalings of (3.9), so it is
+ * self-adjoint in the Frobenius inner product: the adjoint is the same ADI with
+ * the same shifts applied to dL/dX.  Nothing from the forward solve is needed.
+ * Errors as the corresponding solve.
+ */
+int fps_poisson_adjoint(fps_plan *plan, const double *dLdX, double *dLdF);
+
+/* Fill *info.  Errors: INVALID_ARG. */
+int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info);
+
+/*
+ * fps_plan_shifts -- copy the plan's ADI shifts q_0..q_{J-1} (for the square,
+ * p_j = -q_j) into q (capacity `cap`); returns the count written or a negative
+ * status.  For a batch, the shifts of problem `problem`.
+ */
+int fps_plan_shifts(const fps_plan *plan, int64_t problem, double *q, int cap);
+
+/* Release every resource of the plan (synchronises its stream).  NULL is a no-op. */
+void fps_plan_destroy(fps_plan *plan);
+
+/* Static one-line description of a status code. */
+const char *fps_status_string(int status);
+
+/* Message describing the most recent error on the calling thread ("" if none). */
+const char *fps_last_error(void);
+
+/* ---------------- host-only helpers (no GPU needed) ---------------- */
+
+/*
+ * fps_zolotarev_shifts -- ADI shifts of Theorem 2.1 for A X - X B = F with
+ * sigma(A) in [a,b], sigma(B) in [c,d], a < b < c < d, 0 < tol < 1.
+ * J <= 0 selects J from (2.9).  Writes *J_out; if p and q are non-NULL they
+ * receive J values each (capacity `cap`).  Computed in FP64 on the host.
+ * Errors: INVALID_ARG (interval order, tol, capacity too small).
+ */
+int fps_zolotarev_shifts(double a, double b, double c, double d, double tol, int J, int *J_out, double *p, double *q,
+                         int cap);
+
+/*
+ * fps_square_bands -- the symmetric A~ of (3.9) for size n: diagonal d[0..n-1]
+ * and coupling e[j] = A~[j][j+2] for j < n-2.  Host FP64.  Errors: INVALID_ARG.
+ */
+int fps_square_bands(int64_t n, double *d, double *e);
+
+/* Build identification (compute capability the kernels were built for, e.g. 103). */
+int fps_build_arch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPS_H */

@@ -1,0 +1,259 @@
+"""Thin Python binding of the C ABI in ``include/fps.h`` (argument marshalling only).
+
+Every function here forwards to ``libfps.so``; all arithmetic of the solve runs
+in the library's CUDA kernels.  Tensors are passed as raw pointers: a CUDA
+tensor is used in place (asynchronous on the plan's stream), a NumPy array or
+CPU tensor is staged by the library itself.  If the library has not been built
+the first call raises; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfps.so")
+
+FPS_FP64 = 0
+FPS_FP32_REFINE = 1
+_PRECISION = {"fp64": FPS_FP64, "fp32_refine": FPS_FP32_REFINE, FPS_FP64: FPS_FP64, FPS_FP32_REFINE: FPS_FP32_REFINE}
+
+STATUS = {
+    0: "FPS_OK",
+    -1: "FPS_ERR_INVALID_ARG",
+    -2: "FPS_ERR_UNSUPPORTED",
+    -3: "FPS_ERR_CUDA",
+    -4: "FPS_ERR_NOT_CONVERGED",
+    -5: "FPS_ERR_NONFINITE",
+    -6: "FPS_ERR_TIMEOUT",
+}
+
+
+class FpsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("dim", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("nrhs", ctypes.c_int),
+        ("batch", ctypes.c_int64),
+        ("J", ctypes.c_int),
+        ("J_inner", ctypes.c_int),
+        ("refine_rounds", ctypes.c_int),
+        ("last_residual", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("device_bytes", ctypes.c_int64),
+    ]
+
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+EXPORTED = [
+    "fps_plan_create", "fps_plan_create_batched", "fps_plan_set_stream", "fps_poisson_square_solve",
+    "fps_poisson_cube_solve", "fps_poisson_adjoint", "fps_plan_info", "fps_plan_shifts", "fps_plan_destroy",
+    "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
+]
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libfps.so`` (built by ``build_ext.build()``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise FpsError(-3, f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        L.fps_plan_create.argtypes = [ctypes.POINTER(vp), i64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_int, vp]
+        L.fps_plan_create_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, ctypes.c_int,
+                                              ctypes.c_double, ctypes.c_int, vp]
+        L.fps_plan_set_stream.argtypes = [vp, vp]
+        L.fps_poisson_square_solve.argtypes = [vp, vp, vp]
+        L.fps_poisson_cube_solve.argtypes = [vp, vp, vp]
+        L.fps_poisson_adjoint.argtypes = [vp, vp, vp]
+        L.fps_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        L.fps_plan_shifts.argtypes = [vp, i64, dp, ctypes.c_int]
+        L.fps_plan_destroy.argtypes = [vp]
+        L.fps_plan_destroy.restype = None
+        L.fps_status_string.argtypes = [ctypes.c_int]
+        L.fps_status_string.restype = ctypes.c_char_p
+        L.fps_last_error.restype = ctypes.c_char_p
+        L.fps_zolotarev_shifts.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
+                                                                   dp, ctypes.c_int]
+        L.fps_square_bands.argtypes = [i64, dp, dp]
+        _lib = L
+        return L
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        raise FpsError(status, lib().fps_last_error().decode())
+    return status
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr(x) -> int:
+    """Raw pointer of a contiguous FP64 tensor/array (marshalling only)."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise FpsError(-1, "arrays must be contiguous float64")
+        return x.ctypes.data
+    import torch
+
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise FpsError(-1, "tensors must be contiguous float64")
+        return x.data_ptr()
+    raise FpsError(-1, f"unsupported buffer type {type(x)}")
+
+
+def _current_stream() -> int:
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:  # pragma: no cover
+        pass
+    return 0
+
+
+class Plan:
+    """Owning handle of an ``fps_plan``."""
+
+    def __init__(self, handle: int, n: int, dim: int, nrhs: int, batch_ns=None):
+        self._h = ctypes.c_void_p(handle)
+        self.n, self.dim, self.nrhs = n, dim, nrhs
+        self.batch_ns = batch_ns
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise FpsError(-1, "plan already destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        return plan_info(self)
+
+    def destroy(self) -> None:
+        plan_destroy(self)
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            if self._h:
+                plan_destroy(self)
+        except Exception:
+            pass
+
+    def shape(self):
+        if self.batch_ns is not None:
+            return (int(sum(self.nrhs * int(m) ** 2 for m in self.batch_ns)),)
+        if self.dim == 2:
+            return (self.nrhs, self.n, self.n) if self.nrhs > 1 else (self.n, self.n)
+        return (self.nrhs, self.n, self.n, self.n) if self.nrhs > 1 else (self.n, self.n, self.n)
+
+
+# ---------------------------------------------------------------- the C ABI, by name
+def plan_create(n: int, dim: int = 2, tol: float = 1e-13, precision="fp64", nrhs: int = 1,
+                stream: Optional[int] = None) -> Plan:
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else int(stream)
+    _check(lib().fps_plan_create(ctypes.byref(h), int(n), int(dim), float(tol), _PRECISION[precision], int(nrhs),
+                                 ctypes.c_void_p(s)))
+    return Plan(h.value, int(n), int(dim), int(nrhs))
+
+
+def plan_create_batched(ns, nrhs: int = 1, tol: float = 1e-10, precision="fp32_refine",
+                        stream: Optional[int] = None) -> Plan:
+    arr = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else int(stream)
+    _check(lib().fps_plan_create_batched(ctypes.byref(h), arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         len(arr), int(nrhs), float(tol), _PRECISION[precision],
+                                         ctypes.c_void_p(s)))
+    return Plan(h.value, int(arr.max()), 2, int(nrhs), batch_ns=arr)
+
+
+def plan_set_stream(plan: Plan, stream: int) -> None:
+    _check(lib().fps_plan_set_stream(plan.handle, ctypes.c_void_p(int(stream))))
+
+
+def _out_like(F, X):
+    if X is not None:
+        return X
+    if isinstance(F, np.ndarray):
+        return np.empty_like(F)
+    import torch
+
+    return torch.empty_like(F)
+
+
+def poisson_square_solve(plan: Plan, F, X=None):
+    X = _out_like(F, X)
+    _check(lib().fps_poisson_square_solve(plan.handle, ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(_ptr(X))))
+    return X
+
+
+def poisson_cube_solve(plan: Plan, F, X=None):
+    X = _out_like(F, X)
+    _check(lib().fps_poisson_cube_solve(plan.handle, ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(_ptr(X))))
+    return X
+
+
+def poisson_adjoint(plan: Plan, dLdX, dLdF=None):
+    dLdF = _out_like(dLdX, dLdF)
+    _check(lib().fps_poisson_adjoint(plan.handle, ctypes.c_void_p(_ptr(dLdX)), ctypes.c_void_p(_ptr(dLdF))))
+    return dLdF
+
+
+def plan_info(plan: Plan) -> dict:
+    info = PlanInfo()
+    _check(lib().fps_plan_info(plan.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in PlanInfo._fields_}
+
+
+def plan_shifts(plan: Plan, problem: int = 0) -> np.ndarray:
+    cap = 4096
+    q = np.zeros(cap)
+    J = _check(lib().fps_plan_shifts(plan.handle, int(problem), _dp(q), cap))
+    return q[:J].copy()
+
+
+def plan_destroy(plan: Plan) -> None:
+    if plan._h:
+        lib().fps_plan_destroy(plan._h)
+        plan._h = ctypes.c_void_p()
+
+
+def zolotarev_shifts(a: float, b: float, c: float, d: float, tol: float, J: int = 0):
+    Jo = ctypes.c_int()
+    _check(lib().fps_zolotarev_shifts(a, b, c, d, tol, int(J), ctypes.byref(Jo), None, None, 0))
+    p, q = np.zeros(Jo.value), np.zeros(Jo.value)
+    _check(lib().fps_zolotarev_shifts(a, b, c, d, tol, int(J), ctypes.byref(Jo), _dp(p), _dp(q), Jo.value))
+    return p, q
+
+
+def square_bands(n: int):
+    d = np.zeros(n)
+    e = np.zeros(max(n - 2, 1))
+    _check(lib().fps_square_bands(int(n), _dp(d), _dp(e)))
+    return d, e[: max(n - 2, 0)]
+
+
+def status_string(status: int) -> str:
+    return lib().fps_status_string(int(status)).decode()

@@ -1,0 +1,29 @@
+// Host-side FP64 mathematics of the solver: the symmetric matrix A~ of (3.9),
+// the spectral interval of Lemma B.2, the iteration count (2.9) and the
+// Zolotarev shifts (2.4).  Internal header of the library.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace fps {
+
+// A~ = -E^{-1/2} M E^{-1/2}, E = diag((j+1)(j+2)): diag d (n) and e[j] = A~[j][j+2]
+// (padded to length n with zeros so that e[j] = 0 for j+2 >= n).
+void square_bands(int64_t n, std::vector<double> &d, std::vector<double> &e);
+
+// 1/sqrt(E_j), j < n: the diagonal D_s of (3.9) (D_s = |D|^{-1/2}).
+void inv_sqrt_E(int64_t n, std::vector<double> &s);
+
+// Lemma B.2 lower end of |sigma(A~)|: 1/(30 n^4).
+double square_eps(int64_t n);
+
+// J = ceil(log(16 gamma) log(4/tol) / pi^2), gamma the cross-ratio of [a,b], [c,d].
+int adi_iterations(double a, double b, double c, double d, double tol);
+
+// Shifts p_j in [a,b] and q_j in [c,d] of (2.4) for J iterations.
+void zolotarev_shifts(double a, double b, double c, double d, int J, std::vector<double> &p, std::vector<double> &q);
+
+// Symmetric case [a,b] = [-hi,-lo], [c,d] = [lo,hi]: q_j = hi * dn(u_j; k' = lo/hi), p_j = -q_j.
+void zolotarev_shifts_symmetric(double lo, double hi, int J, std::vector<double> &q);
+
+}  // namespace fps

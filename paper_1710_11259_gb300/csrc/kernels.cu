@@ -1,0 +1,206 @@
+// sm_103a kernels of the square ADI solve (Algorithm 2 on the symmetrised
+// equation (3.9); banded shifted solves by the Thomas algorithm on the even and
+// odd index sets, App. B / P3).  The work is HBM/ALU bound streaming with a
+// sequential recurrence per system; there is no dense contraction, so no tensor
+// cores are involved.
+#include "kernels.cuh"
+
+namespace fps {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCols = 32;   // columns per CTA (one warp per row parity)
+constexpr int kTR = 32;     // rows per transposed-store tile
+
+template <typename T> struct Pair;
+template <> struct Pair<double> { using type = double2; };
+template <> struct Pair<float> { using type = float2; };
+
+// ---------------------------------------------------------------------------
+// Half-step kernel.  CTA = 2 warps over 32 consecutive columns k0..k0+31;
+// warp `par` owns the rows i = par, par+2, ... of those columns.
+//   forward:  r_i = G[i,k] - (e_{k-2} V[i,k-2] + (d_k+q) V[i,k] + e_k V[i,k+2])
+//             z_i = r_i - uf_{i-2} z_{i-2}          (spilled to Z)
+//   backward: x_i = ip_i z_i - uf_i x_{i+2}
+// The backward results are staged in a shared-memory tile and stored
+// transposed (Out[k*n + i]) so that the next half-step reads them row-wise.
+// ---------------------------------------------------------------------------
+template <typename T, bool ZERO_V, bool TRANS>
+__global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, const T *__restrict__ G,
+                                                      T *__restrict__ Z, T *__restrict__ Out,
+                                                      const typename Pair<T>::type *__restrict__ fac,
+                                                      const T *__restrict__ dband, const T *__restrict__ eband, T q,
+                                                      int64_t n)
+{
+    __shared__ T tile[kCols][kTR + 1];
+    const int lane = threadIdx.x & 31;
+    const int par = threadIdx.x >> 5;
+    const int64_t k0 = (int64_t)blockIdx.x * kCols;
+    const int64_t k = k0 + lane;
+    const bool kin = k < n;
+
+    T em = 0, c0 = 0, ep = 0;
+    if (kin) {
+        c0 = dband[k] + q;
+        if (k >= 2) em = eband[k - 2];
+        ep = eband[k];  // zero-padded: e[k] = 0 when k + 2 >= n
+    }
+    const int64_t m = (n - par + 1) / 2;  // rows of this parity
+
+    // ---------------- forward elimination ----------------
+    T z = 0;
+    for (int64_t t = 0; t < m; ++t) {
+        const int64_t i = par + 2 * t;
+        const int64_t row = i * n;
+        T r = kin ? G[row + k] : T(0);
+        if (!ZERO_V) {
+            T v0 = kin ? V[row + k] : T(0);
+            T vm = __shfl_up_sync(kFull, v0, 2);
+            T vp = __shfl_down_sync(kFull, v0, 2);
+            if (lane < 2) vm = (kin && k >= 2) ? V[row + k - 2] : T(0);
+            if (lane >= 30) vp = (k + 2 < n) ? V[row + k + 2] : T(0);
+            r = fma(-em, vm, r);
+            r = fma(-c0, v0, r);
+            r = fma(-ep, vp, r);
+        }
+        if (t > 0) z = fma(-fac[i - 2].y, z, r);
+        else z = r;
+        if (kin) Z[row + k] = z;
+    }
+
+    // ---------------- backward substitution ----------------
+    T x = 0;
+    if (!TRANS) {
+        for (int64_t t = m - 1; t >= 0; --t) {
+            const int64_t i = par + 2 * t;
+            const typename Pair<T>::type f = fac[i];
+            const T zz = kin ? Z[i * n + k] : T(0);
+            x = fma(-f.y, x, f.x * zz);
+            if (kin) Out[i * n + k] = x;
+        }
+        return;
+    }
+    const int64_t ntile = (n + kTR - 1) / kTR;
+    for (int64_t b = ntile - 1; b >= 0; --b) {
+        const int64_t ilo = b * kTR;
+        const int64_t ihi = (ilo + kTR < n) ? ilo + kTR : n;
+        int64_t istart = ihi - 1;
+        if (((istart - par) & 1) != 0) --istart;
+        for (int64_t i = istart; i >= ilo; i -= 2) {
+            const typename Pair<T>::type f = fac[i];
+            const T zz = kin ? Z[i * n + k] : T(0);
+            x = fma(-f.y, x, f.x * zz);
+            tile[lane][i - ilo] = x;
+        }
+        __syncthreads();
+        const int rows = (int)(ihi - ilo);
+        for (int idx = threadIdx.x; idx < kCols * kTR; idx += 64) {
+            const int c = idx / kTR, rr = idx % kTR;
+            if (k0 + c < n && rr < rows) Out[(k0 + c) * n + ilo + rr] = tile[c][rr];
+        }
+        __syncthreads();
+    }
+}
+
+// Thomas factors of A~ - q_j I for one (shift, parity) per thread.
+__global__ void factor_kernel(const double *__restrict__ d, const double *__restrict__ e, const double *__restrict__ q,
+                              int J, int64_t n, double2 *__restrict__ fac, float2 *__restrict__ fac32)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= 2 * J) return;
+    const int j = tid >> 1, par = tid & 1;
+    const double qj = q[j];
+    double uf_prev = 0.0;
+    for (int64_t i = par; i < n; i += 2) {
+        double den = d[i] - qj;
+        if (i >= 2) den -= e[i - 2] * uf_prev;
+        const double ip = 1.0 / den;
+        const double uf = e[i] * ip;
+        fac[(int64_t)j * n + i] = make_double2(ip, uf);
+        if (fac32) fac32[(int64_t)j * n + i] = make_float2((float)ip, (float)uf);
+        uf_prev = uf;
+    }
+}
+
+// F~ = D_s F D_s and F~^T through a 32x32 shared tile.
+__global__ void scale_in_kernel(const double *__restrict__ F, double *__restrict__ Ft, double *__restrict__ FtT,
+                                const double *__restrict__ s, int64_t n)
+{
+    __shared__ double t[32][33];
+    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = by + r, k = bx + threadIdx.x;
+        if (i < n && k < n) {
+            const double v = F[i * n + k] * s[i] * s[k];
+            Ft[i * n + k] = v;
+            t[r][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t k = bx + r, i = by + threadIdx.x;
+        if (i < n && k < n) FtT[k * n + i] = t[threadIdx.x][r];
+    }
+}
+
+__global__ void scale_out_kernel(const double *__restrict__ Y, double *__restrict__ X, const double *__restrict__ s,
+                                 int64_t n)
+{
+    const int64_t nn = n * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / n, k = t - i * n;
+        X[t] = Y[t] * s[i] * s[k];
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_halfstep(const HalfStep<T> &h, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((h.n + kCols - 1) / kCols)), block(64);
+    using P = typename Pair<T>::type;
+    const P *fac = static_cast<const P *>(h.fac);
+    if (h.V == nullptr) {
+        if (h.transposed_out)
+            halfstep_kernel<T, true, true><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+        else
+            halfstep_kernel<T, true, false><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+    } else {
+        if (h.transposed_out)
+            halfstep_kernel<T, false, true><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+        else
+            halfstep_kernel<T, false, false><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_halfstep<double>(const HalfStep<double> &, cudaStream_t);
+template cudaError_t launch_halfstep<float>(const HalfStep<float> &, cudaStream_t);
+
+cudaError_t launch_factors(const double *d, const double *e, const double *q, int J, int64_t n, double2 *fac,
+                           float2 *fac32, cudaStream_t st)
+{
+    const int threads = 2 * J;
+    factor_kernel<<<(threads + 127) / 128, 128, 0, st>>>(d, e, q, J, n, fac, fac32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_in(const double *F, double *Ft, double *FtT, const double *s, int64_t n, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+    scale_in_kernel<<<grid, block, 0, st>>>(F, Ft, FtT, s, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_out(const double *Y, double *X, const double *s, int64_t n, cudaStream_t st)
+{
+    const int64_t nn = n * n;
+    int blocks = (int)((nn + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    scale_out_kernel<<<blocks, 256, 0, st>>>(Y, X, s, n);
+    return cudaGetLastError();
+}
+
+}  // namespace fps

@@ -1,0 +1,121 @@
+"""CPU checks of the C-ABI library: it loads without a GPU, exports every
+function declared in include/fps.h, and its host-side mathematics (bands of A~,
+Zolotarev shifts, J) agrees with the oracle and with mpmath."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_11259_gb300 import api, build_ext
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build_ext.build()
+    return api.lib()
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(fps_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(L):
+    declared = _declared_functions()
+    assert "fps_plan_create" in declared and "fps_poisson_square_solve" in declared
+    for name in declared:
+        assert hasattr(L, name), f"{name} declared in include/ but not exported"
+    assert set(api.EXPORTED) <= set(declared)
+
+
+def test_build_arch(L):
+    assert L.fps_build_arch() == 103
+
+
+def test_status_strings(L):
+    assert api.status_string(0) == "ok"
+    assert api.status_string(-4) == "refinement did not converge"
+
+
+def test_argument_errors_without_gpu(L):
+    """Argument checks run before any CUDA call."""
+    with pytest.raises(api.FpsError) as e:
+        api.plan_create(0)
+    assert e.value.status == -1
+    with pytest.raises(api.FpsError) as e:
+        api.plan_create(16, tol=1.5)
+    assert e.value.status == -1
+    with pytest.raises(api.FpsError) as e:
+        api.plan_create(16, dim=4)
+    assert e.value.status == -1
+    with pytest.raises(api.FpsError):
+        api.zolotarev_shifts(1.0, 0.0, 2.0, 3.0, 1e-6)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 1001])
+def test_square_bands_match_oracle(L, n):
+    d, e = api.square_bands(n)
+    do, eo = oracle.square_bands(n)
+    assert np.abs(d - do).max() <= 1e-15 * np.abs(do).max()
+    if n > 2:
+        assert np.abs(e - eo).max() <= 1e-15 * np.abs(eo).max()
+
+
+@pytest.mark.parametrize("n", [1, 16, 64, 512, 2048, 4096, 10000])
+@pytest.mark.parametrize("tol", [1e-13, 1e-10, 1e-7])
+def test_iteration_count_matches_oracle(L, n, tol):
+    a, b, c, d = oracle.square_interval(n)
+    p, q = api.zolotarev_shifts(a, b, c, d, tol)
+    assert len(q) == oracle.adi_iterations(a, b, c, d, tol)
+
+
+@pytest.mark.parametrize("case", ["square64", "square4096", "square10000", "fd64", "asym", "cube_outer"])
+def test_library_shifts_against_mpmath(L, case):
+    """The library's own elliptic-function route to (2.4) against mpmath."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    if case.startswith("square"):
+        a, b, c, d = oracle.square_interval(int(case[6:]))
+    elif case == "fd64":
+        a, b, c, d = -4096.0, -1.0, 1.0, 4096.0
+    elif case == "asym":
+        a, b, c, d = -1.0, -1e-10, 2e-10, 2.0
+    else:
+        e2 = (1.0 / (30.0 * 256.0**4)) ** 2
+        a, b, c, d = -1.0, -e2, 2 * e2, 2.0
+    p, q = api.zolotarev_shifts(a, b, c, d, 1e-13)
+    J = len(q)
+    A, B, C, D = (mp.mpf(v) for v in (a, b, c, d))
+    gam = abs(C - A) * abs(D - B) / (abs(C - B) * abs(D - A))
+    alp = -1 + 2 * gam + 2 * mp.sqrt(gam**2 - gam)
+    m = 1 - 1 / alp**2
+    K = mp.ellipk(m)
+
+    def T(z):
+        s = (z + alp) * (-2) / ((z - 1) * (alp - 1))
+        return (s * C * (B - A) - A * (B - C)) / (s * (B - A) - (B - C))
+
+    worst = 0.0
+    for j in range(J):
+        dn = mp.ellipfun("dn", (j + mp.mpf(1) / 2) * K / J, m=m)
+        for got, want in ((p[j], T(-alp * dn)), (q[j], T(alp * dn))):
+            worst = max(worst, float(abs(got - want) / abs(want)))
+    assert worst < 1e-12, worst
+
+
+def test_library_and_oracle_shifts_agree(L):
+    for n in (64, 4096, 10000):
+        a, b, c, d = oracle.square_interval(n)
+        po, qo = oracle.adi_shifts(a, b, c, d, 1e-13)
+        p, q = api.zolotarev_shifts(a, b, c, d, 1e-13)
+        assert np.abs(q - qo).max() / 1.0 < 1e-13
+        assert (np.abs(q - qo) / qo).max() < 1e-12

@@ -1,0 +1,128 @@
+"""GPU parity of the square solve (FP64) against the CPU oracle, through the C ABI.
+
+Tolerance: relative max-coefficient error max|X_gpu - X_orc| / max|X_orc| <= 1e-12,
+the FP64 bar of the workload definition.  Both sides run the same J and shifts;
+only the rounding order differs."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import basis
+from paper_1710_11259_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+
+
+def _relmax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_11259_gb300 import api as _api
+    from paper_1710_11259_gb300 import build_ext
+
+    build_ext.build()
+    _api.lib()
+    return _api
+
+
+def _solve(api, F, tol=1e-13, precision="fp64"):
+    plan = api.plan_create(F.shape[-1], 2, tol, precision, nrhs=1 if F.ndim == 2 else F.shape[0])
+    Fd = torch.from_numpy(F).cuda()
+    X = api.poisson_square_solve(plan, Fd)
+    torch.cuda.synchronize()
+    info = api.plan_info(plan)
+    api.plan_destroy(plan)
+    return X.cpu().numpy(), info
+
+
+# n spans: degenerate (1, 2, 3), odd/even parity lengths, a ragged 32-column CTA
+# tail and a ragged 32-row store tile (33, 65, 100, 257), several tiles (64, 257).
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 31, 32, 33, 64, 65, 100, 257])
+def test_square_fp64_matches_oracle(api, n):
+    F = inputs.square_rhs(n, 100 + n)
+    X, info = _solve(api, F)
+    Xo = oracle.poisson_square(F, 1e-13)
+    assert info["J"] == oracle.square_iterations(n, 1e-13)
+    assert _relmax(X, Xo) <= TOL_FP64
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-7, 1e-10])
+def test_square_fp64_other_tolerances(api, tol):
+    n = 96
+    F = inputs.square_rhs(n, 7, power=1)
+    X, _ = _solve(api, F, tol)
+    Xo = oracle.poisson_square(F, tol)
+    assert _relmax(X, Xo) <= TOL_FP64
+
+
+def test_config_small_random_and_manufactured(api):
+    """n = 64: RHS 1 = g/((1+j)^2(1+k)^2) (seed 0); RHS 2 from the manufactured
+    u = (1-x^2)(1-y^2)p, deg p <= 10 (seed 1); both against the oracle and the
+    dense Kronecker solve / exact coefficients."""
+    n = 64
+    F1 = inputs.square_rhs(n, 0)
+    pc = basis.monomial_coeffs(inputs.poly_values(1), 10)
+    F2, Xexact = basis.manufactured_square(pc, n)
+    F = np.stack([F1, F2])
+    X, info = _solve(api, F)
+    assert info["nrhs"] == 2 and info["J"] == 68
+    for r in range(2):
+        assert _relmax(X[r], oracle.poisson_square(F[r], 1e-13)) <= TOL_FP64
+    assert _relmax(X[1], Xexact) <= 2e-13
+    # dense Kronecker check of RHS 1
+    d, e = oracle.M_bands(n)
+    M = np.diag(d)
+    for j in range(n - 2):
+        M[j, j + 2] = M[j + 2, j] = e[j]
+    Dm = np.diag([-(j * (j + 3) + 2.0) for j in range(n)])
+    Xd = np.linalg.solve(np.kron(M, Dm) + np.kron(Dm, M), F1.ravel()).reshape(n, n)
+    assert _relmax(X[0], Xd) <= 2e-13
+
+
+def test_host_pointer_path_equals_device_path(api):
+    n = 77
+    F = inputs.square_rhs(n, 9)
+    plan = api.plan_create(n, 2, 1e-13, "fp64")
+    Xh = api.poisson_square_solve(plan, F)          # numpy in, numpy out: staged by the library
+    Xd = api.poisson_square_solve(plan, torch.from_numpy(F).cuda()).cpu().numpy()
+    api.plan_destroy(plan)
+    assert np.array_equal(Xh, Xd)
+
+
+def test_repeat_is_bitwise_deterministic(api):
+    n = 200
+    F = torch.from_numpy(inputs.square_rhs(n, 10)).cuda()
+    plan = api.plan_create(n, 2, 1e-13, "fp64")
+    X1 = api.poisson_square_solve(plan, F).clone()
+    X2 = api.poisson_square_solve(plan, F)
+    torch.cuda.synchronize()
+    api.plan_destroy(plan)
+    assert torch.equal(X1, X2)
+
+
+def test_square_fp64_full_size_4096(api):
+    """n = 4096 (16.8M DOF), F = g/((1+j)^2(1+k)^2) seed 2, FP64 tol 1e-13: whole-matrix parity."""
+    n = 4096
+    F = inputs.square_rhs(n, 2)
+    X, info = _solve(api, F)
+    assert info["J"] == 121
+    Xo = oracle.poisson_square(F, 1e-13)
+    assert _relmax(X, Xo) <= TOL_FP64
+
+
+def test_square_fp64_full_size_10000(api):
+    """n = 10^4 (1e8 DOF), F = g/((1+j)(1+k)) seed 3, FP64 tol 1e-13: whole-matrix parity
+    against the oracle run in full on the host cores."""
+    n = 10000
+    F = inputs.square_rhs(n, 3, power=1)
+    X, info = _solve(api, F)
+    assert info["J"] == 133
+    Xo = oracle.poisson_square(F, 1e-13)
+    assert _relmax(X, Xo) <= TOL_FP64
