@@ -10,6 +10,7 @@
 #include "../../include/fps.h"
 #include "host_math.h"
 #include "kernels.cuh"
+#include "refine.cuh"
 
 namespace {
 
@@ -75,6 +76,27 @@ struct fps_plan {
     cudaGraphExec_t graph = nullptr;
     int refine_rounds = 0;
     double last_residual = 0;
+
+    // FPS_FP32_REFINE: FP32 inner ADI (residual-propagating form) per tolerance level
+    struct Level {
+        double tol = 0;
+        int J = 0;
+        std::vector<double> q;
+        double *d_q = nullptr;
+        float4 *fac = nullptr;      // J x n
+        float *phick = nullptr;     // J x 2 x nchunk
+        float4 *segc = nullptr;     // J x 2 x P
+        cudaGraphExec_t graph = nullptr;
+    };
+    fps::RefineGeometry geo;
+    fps::RefineScratch scr;
+    std::vector<Level> levels;
+    int64_t ld = 0;                    // padded leading dimension of the FP32 arrays
+    double *Y0 = nullptr, *Y1 = nullptr;
+    float *Pt = nullptr, *Ar = nullptr, *Cr = nullptr, *Dl = nullptr;
+    unsigned long long *d_scal = nullptr;   // [0] = max|F~| (scale), [1] = max|R~| (bit patterns)
+    unsigned long long *h_scal = nullptr;   // pinned mirror
+    int max_rounds = 8;
 };
 
 namespace {
@@ -92,9 +114,18 @@ void release(fps_plan *p)
     if (!p) return;
     DeviceGuard g(p->device);
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    void *bufs[] = {p->d_d, p->d_e, p->d_s, p->d_q, p->d_fac, p->Ft, p->FtT, p->A, p->B, p->Z};
+    void *bufs[] = {p->d_d, p->d_e, p->d_s, p->d_q, p->d_fac, p->Ft, p->FtT, p->A, p->B, p->Z,
+                    p->Y0, p->Y1, p->Pt, p->Ar, p->Cr, p->Dl, p->scr.ck, p->scr.summ, p->d_scal};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (auto &L : p->levels) {
+        if (L.graph) cudaGraphExecDestroy(L.graph);
+        if (L.d_q) cudaFree(L.d_q);
+        if (L.fac) cudaFree(L.fac);
+        if (L.phick) cudaFree(L.phick);
+        if (L.segc) cudaFree(L.segc);
+    }
+    if (p->h_scal) cudaFreeHost(p->h_scal);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
 }
@@ -147,9 +178,96 @@ int build_graph(fps_plan *p)
     return FPS_OK;
 }
 
+// Capture the inner ADI of one tolerance level: J x (row pass, column pass).
+int build_level_graph(fps_plan *p, fps_plan::Level &L)
+{
+    FPS_CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < L.J && e == cudaSuccess; ++j) {
+        const float q2 = (float)(2.0 * L.q[j]);
+        const float4 *fac = L.fac + (int64_t)j * p->n;
+        const float *phick = L.phick + (int64_t)j * 2 * p->geo.nchunk;
+        const float4 *segc = L.segc + (int64_t)j * 2 * p->geo.P;
+        e = fps::launch_row_pass(p->Pt, p->Ar, p->Cr, p->scr, fac, phick, segc, q2, p->n, p->geo, p->cap_stream);
+        if (e == cudaSuccess)
+            e = fps::launch_col_pass(p->Cr, p->Ar, p->Dl, p->Pt, p->scr, fac, phick, segc, q2, p->n, p->geo, j == 0,
+                                     p->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(FPS_ERR_CUDA, std::string("refine graph capture: ") + cudaGetErrorString(e));
+    }
+    FPS_CK(e2);
+    e = cudaGraphInstantiate(&L.graph, g, 0);
+    cudaGraphDestroy(g);
+    FPS_CK(e);
+    return FPS_OK;
+}
+
+double bits_to_double(unsigned long long b)
+{
+    double d;
+    std::memcpy(&d, &b, sizeof(d));
+    return d;
+}
+
+// FP32 sweeps + FP64 refinement for one right-hand side (device pointers).
+int solve_one_refine(fps_plan *p, const double *F, double *X)
+{
+    cudaStream_t st = p->stream;
+    const int64_t n = p->n;
+    FPS_CK(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(unsigned long long), st));
+    FPS_CK(fps::launch_absmax_scaled(F, p->d_s, n, p->d_scal, st));
+    FPS_CK(cudaMemcpyAsync(p->h_scal, p->d_scal, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    FPS_CK(cudaStreamSynchronize(st));
+    const double sF = bits_to_double(p->h_scal[0]);
+    if (!std::isfinite(sF)) return fail(FPS_ERR_NONFINITE, "fps_poisson_square_solve: F holds NaN or Inf");
+    if (sF == 0.0) {
+        FPS_CK(cudaMemsetAsync(X, 0, sizeof(double) * n * n, st));
+        p->refine_rounds = 0;
+        p->last_residual = 0.0;
+        return FPS_OK;
+    }
+    FPS_CK(fps::launch_refine_scale_in(F, p->Ft, p->Pt, p->d_s, n, p->ld, p->d_scal, st));
+    double rel = 1.0;
+    double *Ycur = p->Y0, *Ynext = p->Y1;
+    bool converged = false;
+    int round = 0;
+    for (; round < p->max_rounds; ++round) {
+        // inner tolerance: aim one decade below what this round must gain
+        const double want = 0.1 * p->tol / rel;
+        size_t li = 0;
+        for (size_t l = 0; l < p->levels.size(); ++l)
+            if (p->levels[l].tol <= want) li = l;
+        FPS_CK(cudaGraphLaunch(p->levels[li].graph, st));
+        FPS_CK(cudaMemsetAsync(p->d_scal + 1, 0, sizeof(unsigned long long), st));
+        FPS_CK(fps::launch_residual(Ycur, Ynext, p->Dl, p->Ft, p->Pt, p->d_d, p->d_e, p->d_scal, n, p->ld,
+                                    p->d_scal + 1, true, round == 0, st));
+        FPS_CK(cudaMemcpyAsync(p->h_scal + 1, p->d_scal + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        FPS_CK(cudaStreamSynchronize(st));
+        std::swap(Ycur, Ynext);
+        const double r = bits_to_double(p->h_scal[1]) / sF;
+        if (!std::isfinite(r)) return fail(FPS_ERR_NONFINITE, "fps_poisson_square_solve: non-finite residual");
+        rel = r;
+        if (rel <= p->tol) {
+            converged = true;
+            ++round;
+            break;
+        }
+    }
+    p->refine_rounds = round;
+    p->last_residual = rel;
+    FPS_CK(fps::launch_scale_out(Ycur, X, p->d_s, n, st));
+    if (!converged) return fail(FPS_ERR_NOT_CONVERGED, "fps_poisson_square_solve: refinement did not reach tol");
+    return FPS_OK;
+}
+
 // One right-hand side, device pointers.
 int solve_one(fps_plan *p, const double *F, double *X)
 {
+    if (p->precision == FPS_FP32_REFINE) return solve_one_refine(p, F, X);
     cudaStream_t st = p->stream;
     FPS_CK(fps::launch_scale_in(F, p->Ft, p->FtT, p->d_s, p->n, st));
     FPS_CK(cudaGraphLaunch(p->graph, st));
@@ -171,18 +289,22 @@ int solve_square(fps_plan *p, const double *F, double *X, const char *what)
     for (int r = 0; r < p->nrhs; ++r) {
         const double *Fr = F + (int64_t)r * nn;
         double *Xr = X + (int64_t)r * nn;
+        const bool refine = p->precision == FPS_FP32_REFINE;
+        double *stage_in = refine ? p->Y1 : p->B;   // free until the solve overwrites it
+        double *stage_out = refine ? p->Ft : p->A;  // free once the solve has finished with it
         const double *Fd = Fr;
         if (!fdev) {
-            FPS_CK(cudaMemcpyAsync(p->B, Fr, sizeof(double) * nn, cudaMemcpyHostToDevice, p->stream));
-            Fd = p->B;
+            FPS_CK(cudaMemcpyAsync(stage_in, Fr, sizeof(double) * nn, cudaMemcpyHostToDevice, p->stream));
+            Fd = stage_in;
         }
-        double *Xd = xdev ? Xr : p->A;
+        double *Xd = xdev ? Xr : stage_out;
         int s = solve_one(p, Fd, Xd);
-        if (s != FPS_OK) return s;
+        if (s != FPS_OK && s != FPS_ERR_NOT_CONVERGED) return s;
         if (!xdev) {
-            FPS_CK(cudaMemcpyAsync(Xr, p->A, sizeof(double) * nn, cudaMemcpyDeviceToHost, p->stream));
+            FPS_CK(cudaMemcpyAsync(Xr, stage_out, sizeof(double) * nn, cudaMemcpyDeviceToHost, p->stream));
             FPS_CK(cudaStreamSynchronize(p->stream));
         }
+        if (s != FPS_OK) return s;
     }
     if (!fdev && xdev) FPS_CK(cudaStreamSynchronize(p->stream));  // host F must stay valid only until copied
     FPS_CK(cudaGetLastError());
@@ -204,7 +326,6 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     if (precision != FPS_FP64 && precision != FPS_FP32_REFINE)
         return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: unknown precision");
     if (dim == 3) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the cube path is not built yet");
-    if (precision != FPS_FP64) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: FP32_REFINE is not built yet");
 
     fps_plan *p = new fps_plan();
     p->n = n;
@@ -242,20 +363,67 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     PCK(dmalloc(p, &p->d_e, n));
     PCK(dmalloc(p, &p->d_s, n));
     PCK(dmalloc(p, &p->d_q, p->J));
-    PCK(dmalloc(p, &p->d_fac, (size_t)p->J * n));
     PCK(dmalloc(p, &p->Ft, nn));
-    PCK(dmalloc(p, &p->FtT, nn));
-    PCK(dmalloc(p, &p->A, nn));
-    PCK(dmalloc(p, &p->B, nn));
-    PCK(dmalloc(p, &p->Z, nn));
+    if (precision == FPS_FP64) {
+        PCK(dmalloc(p, &p->d_fac, (size_t)p->J * n));
+        PCK(dmalloc(p, &p->FtT, nn));
+        PCK(dmalloc(p, &p->A, nn));
+        PCK(dmalloc(p, &p->B, nn));
+        PCK(dmalloc(p, &p->Z, nn));
+    }
     PCK(cudaMemcpyAsync(p->d_d, d.data(), sizeof(double) * n, cudaMemcpyHostToDevice, p->cap_stream));
     PCK(cudaMemcpyAsync(p->d_e, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice, p->cap_stream));
     PCK(cudaMemcpyAsync(p->d_s, s.data(), sizeof(double) * n, cudaMemcpyHostToDevice, p->cap_stream));
     PCK(cudaMemcpyAsync(p->d_q, p->q.data(), sizeof(double) * p->J, cudaMemcpyHostToDevice, p->cap_stream));
-    PCK(fps::launch_factors(p->d_d, p->d_e, p->d_q, p->J, n, p->d_fac, nullptr, p->cap_stream));
-    PCK(cudaStreamSynchronize(p->cap_stream));
-    int st = build_graph(p);
-    if (st != FPS_OK) return bail(st);
+    if (precision == FPS_FP64) {
+        PCK(fps::launch_factors(p->d_d, p->d_e, p->d_q, p->J, n, p->d_fac, nullptr, p->cap_stream));
+        PCK(cudaStreamSynchronize(p->cap_stream));
+        int st = build_graph(p);
+        if (st != FPS_OK) return bail(st);
+    } else {
+        // FP32 arrays with a leading dimension padded to 32 (128-byte rows for cp.async).
+        if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: FP32_REFINE supports n <= 40000"));
+        int sms = 0;
+        PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+        p->geo = fps::refine_geometry(n, sms);
+        p->ld = p->geo.ld;
+        const size_t nl = (size_t)n * (size_t)p->ld;
+        PCK(dmalloc(p, &p->Y0, nn));
+        PCK(dmalloc(p, &p->Y1, nn));
+        PCK(dmalloc(p, &p->Pt, nl));
+        PCK(dmalloc(p, &p->Ar, nl));
+        PCK(dmalloc(p, &p->Cr, nl));
+        PCK(dmalloc(p, &p->Dl, nl));
+        PCK(dmalloc(p, &p->scr.ck, (size_t)fps::refine_checkpoint_floats(p->geo)));
+        PCK(dmalloc(p, &p->scr.summ, (size_t)fps::refine_summary_float2(p->geo)));
+        PCK(dmalloc(p, &p->d_scal, 2));
+        PCK(cudaMallocHost((void **)&p->h_scal, 2 * sizeof(unsigned long long)));
+        float *zero_bufs[] = {p->Pt, p->Ar, p->Cr, p->Dl};
+        for (float *b : zero_bufs) PCK(cudaMemsetAsync(b, 0, sizeof(float) * nl, p->cap_stream));
+        PCK(fps::refine_setup_kernels());
+        // inner tolerance levels, finest (FP32-limited) first
+        const double level_tols[] = {1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2};
+        for (double lt : level_tols) {
+            fps_plan::Level L;
+            L.tol = lt;
+            L.J = fps::adi_iterations(-1.0, -eps, eps, 1.0, lt);
+            fps::zolotarev_shifts_symmetric(eps, 1.0, L.J, L.q);
+            p->levels.push_back(L);
+        }
+        for (auto &L : p->levels) {
+            PCK(dmalloc(p, &L.d_q, L.J));
+            PCK(dmalloc(p, &L.fac, (size_t)L.J * n));
+            PCK(dmalloc(p, &L.phick, (size_t)L.J * 2 * p->geo.nchunk));
+            PCK(dmalloc(p, &L.segc, (size_t)L.J * 2 * p->geo.P));
+            PCK(cudaMemcpyAsync(L.d_q, L.q.data(), sizeof(double) * L.J, cudaMemcpyHostToDevice, p->cap_stream));
+            PCK(fps::launch_factors32(p->d_d, p->d_e, L.d_q, L.J, n, p->geo, L.fac, L.phick, L.segc, p->cap_stream));
+        }
+        PCK(cudaStreamSynchronize(p->cap_stream));
+        for (auto &L : p->levels) {
+            int st = build_level_graph(p, L);
+            if (st != FPS_OK) return bail(st);
+        }
+    }
 #undef PCK
     *out = p;
     return FPS_OK;
@@ -306,7 +474,7 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->nrhs = plan->nrhs;
     info->batch = 1;
     info->J = plan->J;
-    info->J_inner = 0;
+    info->J_inner = plan->levels.empty() ? 0 : plan->levels[0].J;
     info->refine_rounds = plan->refine_rounds;
     info->last_residual = plan->last_residual;
     info->tol = plan->tol;

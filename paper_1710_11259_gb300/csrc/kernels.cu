@@ -12,10 +12,53 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCols = 32;   // columns per CTA (one warp per row parity)
 constexpr int kTR = 32;     // rows per transposed-store tile
+constexpr int kRing = 16;   // prefetch depth (rows) of the per-warp rings
 
 template <typename T> struct Pair;
 template <> struct Pair<double> { using type = double2; };
 template <> struct Pair<float> { using type = float2; };
+
+// ---------------------------------------------------------------------------
+// Asynchronous global->shared copies (cp.async, per-thread 4/8/16 bytes).  Rows
+// are prefetched D-1 steps ahead of the Thomas recurrence so that the load
+// latency overlaps the sequential elimination; a copy with valid == false
+// zero-fills its destination without reading memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+template <int B>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B),
+                 "r"(valid ? B : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Per-warp prefetch rings.  Forward: G row segment (32), V row segment with a
+// two-column halo on each side (36, padded to 40), factors of the row.
+// Backward: spill row segment (32) and factors.
+template <typename T, int D>
+struct FwdRing {
+    T g[D][32];
+    T v[D][40];
+    typename Pair<T>::type f[D];
+};
+template <typename T, int D>
+struct BwdRing {
+    T z[D][32];
+    typename Pair<T>::type f[D];
+};
+template <typename T, int D>
+union WarpRing {
+    FwdRing<T, D> fw;
+    BwdRing<T, D> bw;
+};
 
 // ---------------------------------------------------------------------------
 // Half-step kernel.  CTA = 2 warps over 32 consecutive columns k0..k0+31;
@@ -26,19 +69,22 @@ template <> struct Pair<float> { using type = float2; };
 // The backward results are staged in a shared-memory tile and stored
 // transposed (Out[k*n + i]) so that the next half-step reads them row-wise.
 // ---------------------------------------------------------------------------
-template <typename T, bool ZERO_V, bool TRANS>
+template <typename T, bool ZERO_V, bool TRANS, int D>
 __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, const T *__restrict__ G,
                                                       T *__restrict__ Z, T *__restrict__ Out,
                                                       const typename Pair<T>::type *__restrict__ fac,
                                                       const T *__restrict__ dband, const T *__restrict__ eband, T q,
                                                       int64_t n)
 {
+    using P = typename Pair<T>::type;
+    __shared__ __align__(16) WarpRing<T, D> rings[2];
     __shared__ T tile[kCols][kTR + 1];
     const int lane = threadIdx.x & 31;
     const int par = threadIdx.x >> 5;
     const int64_t k0 = (int64_t)blockIdx.x * kCols;
     const int64_t k = k0 + lane;
     const bool kin = k < n;
+    WarpRing<T, D> &R = rings[par];
 
     T em = 0, c0 = 0, ep = 0;
     if (kin) {
@@ -49,36 +95,72 @@ __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, c
     const int64_t m = (n - par + 1) / 2;  // rows of this parity
 
     // ---------------- forward elimination ----------------
-    T z = 0;
-    for (int64_t t = 0; t < m; ++t) {
-        const int64_t i = par + 2 * t;
-        const int64_t row = i * n;
-        T r = kin ? G[row + k] : T(0);
-        if (!ZERO_V) {
-            T v0 = kin ? V[row + k] : T(0);
-            T vm = __shfl_up_sync(kFull, v0, 2);
-            T vp = __shfl_down_sync(kFull, v0, 2);
-            if (lane < 2) vm = (kin && k >= 2) ? V[row + k - 2] : T(0);
-            if (lane >= 30) vp = (k + 2 < n) ? V[row + k + 2] : T(0);
-            r = fma(-em, vm, r);
-            r = fma(-c0, v0, r);
-            r = fma(-ep, vp, r);
+    auto issue_fwd = [&](int64_t t) {
+        if (t < m) {
+            const int s = (int)(t % D);
+            const int64_t i = par + 2 * t;
+            cp_async<sizeof(T)>(&R.fw.g[s][lane], kin ? G + i * n + k : G, kin);
+            if (!ZERO_V) {
+                const int64_t kk = k0 - 2 + lane;
+                const bool ok = kk >= 0 && kk < n;
+                cp_async<sizeof(T)>(&R.fw.v[s][lane], ok ? V + i * n + kk : V, ok);
+                if (lane < 4) {
+                    const int64_t kh = k0 + 30 + lane;
+                    const bool okh = kh < n;
+                    cp_async<sizeof(T)>(&R.fw.v[s][32 + lane], okh ? V + i * n + kh : V, okh);
+                }
+            }
+            if (lane == 31) cp_async<sizeof(P)>(&R.fw.f[s], fac + i, true);
         }
-        if (t > 0) z = fma(-fac[i - 2].y, z, r);
-        else z = r;
-        if (kin) Z[row + k] = z;
+        cp_commit();
+    };
+    for (int t = 0; t < D - 1; ++t) issue_fwd(t);
+    T z = 0, uf_prev = 0;
+    for (int64_t t = 0; t < m; ++t) {
+        __syncwarp();
+        issue_fwd(t + D - 1);
+        cp_wait<D - 1>();
+        __syncwarp();
+        const int s = (int)(t % D);
+        T r = R.fw.g[s][lane];
+        if (!ZERO_V) {
+            r = fma(-em, R.fw.v[s][lane], r);
+            r = fma(-c0, R.fw.v[s][lane + 2], r);
+            r = fma(-ep, R.fw.v[s][lane + 4], r);
+        }
+        z = fma(-uf_prev, z, r);
+        uf_prev = R.fw.f[s].y;
+        if (kin) Z[(par + 2 * t) * n + k] = z;
     }
+    cp_wait<0>();
+    __syncwarp();
 
     // ---------------- backward substitution ----------------
-    T x = 0;
-    if (!TRANS) {
-        for (int64_t t = m - 1; t >= 0; --t) {
-            const int64_t i = par + 2 * t;
-            const typename Pair<T>::type f = fac[i];
-            const T zz = kin ? Z[i * n + k] : T(0);
-            x = fma(-f.y, x, f.x * zz);
-            if (kin) Out[i * n + k] = x;
+    // u counts rows from the last one: t = m-1-u.
+    auto issue_bwd = [&](int64_t u) {
+        if (u < m) {
+            const int s = (int)(u % D);
+            const int64_t i = par + 2 * (m - 1 - u);
+            cp_async<sizeof(T)>(&R.bw.z[s][lane], kin ? Z + i * n + k : Z, kin);
+            if (lane == 31) cp_async<sizeof(P)>(&R.bw.f[s], fac + i, true);
         }
+        cp_commit();
+    };
+    for (int u = 0; u < D - 1; ++u) issue_bwd(u);
+    T x = 0;
+    int64_t u = 0;
+    if (!TRANS) {
+        for (; u < m; ++u) {
+            __syncwarp();
+            issue_bwd(u + D - 1);
+            cp_wait<D - 1>();
+            __syncwarp();
+            const int s = (int)(u % D);
+            const P f = R.bw.f[s];
+            x = fma(-f.y, x, f.x * R.bw.z[s][lane]);
+            if (kin) Out[(par + 2 * (m - 1 - u)) * n + k] = x;
+        }
+        cp_wait<0>();
         return;
     }
     const int64_t ntile = (n + kTR - 1) / kTR;
@@ -87,10 +169,14 @@ __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, c
         const int64_t ihi = (ilo + kTR < n) ? ilo + kTR : n;
         int64_t istart = ihi - 1;
         if (((istart - par) & 1) != 0) --istart;
-        for (int64_t i = istart; i >= ilo; i -= 2) {
-            const typename Pair<T>::type f = fac[i];
-            const T zz = kin ? Z[i * n + k] : T(0);
-            x = fma(-f.y, x, f.x * zz);
+        for (int64_t i = istart; i >= ilo; i -= 2, ++u) {
+            __syncwarp();
+            issue_bwd(u + D - 1);
+            cp_wait<D - 1>();
+            __syncwarp();
+            const int s = (int)(u % D);
+            const P f = R.bw.f[s];
+            x = fma(-f.y, x, f.x * R.bw.z[s][lane]);
             tile[lane][i - ilo] = x;
         }
         __syncthreads();
@@ -101,6 +187,7 @@ __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, c
         }
         __syncthreads();
     }
+    cp_wait<0>();
 }
 
 // Thomas factors of A~ - q_j I for one (shift, parity) per thread.
@@ -164,14 +251,14 @@ cudaError_t launch_halfstep(const HalfStep<T> &h, cudaStream_t st)
     const P *fac = static_cast<const P *>(h.fac);
     if (h.V == nullptr) {
         if (h.transposed_out)
-            halfstep_kernel<T, true, true><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+            halfstep_kernel<T, true, true, kRing><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
         else
-            halfstep_kernel<T, true, false><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+            halfstep_kernel<T, true, false, kRing><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
     } else {
         if (h.transposed_out)
-            halfstep_kernel<T, false, true><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+            halfstep_kernel<T, false, true, kRing><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
         else
-            halfstep_kernel<T, false, false><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
+            halfstep_kernel<T, false, false, kRing><<<grid, block, 0, st>>>(h.V, h.G, h.Z, h.Out, fac, h.d, h.e, h.q, h.n);
     }
     return cudaGetLastError();
 }

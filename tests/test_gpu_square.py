@@ -14,6 +14,18 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_FP64 = 1e-12
+TOL_REFINE = 1e-10
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_full(n, seed, power):
+    """Oracle solution of a full-size case, computed once per test session."""
+    key = (n, seed, power)
+    if key not in _ORACLE_CACHE:
+        F = inputs.square_rhs(n, seed, power=power)
+        _ORACLE_CACHE[key] = (F, oracle.poisson_square(F, 1e-13))
+    return _ORACLE_CACHE[key]
 
 
 def _relmax(a, b):
@@ -109,20 +121,62 @@ def test_repeat_is_bitwise_deterministic(api):
 
 def test_square_fp64_full_size_4096(api):
     """n = 4096 (16.8M DOF), F = g/((1+j)^2(1+k)^2) seed 2, FP64 tol 1e-13: whole-matrix parity."""
-    n = 4096
-    F = inputs.square_rhs(n, 2)
+    F, Xo = _oracle_full(4096, 2, 2)
     X, info = _solve(api, F)
     assert info["J"] == 121
-    Xo = oracle.poisson_square(F, 1e-13)
     assert _relmax(X, Xo) <= TOL_FP64
 
 
 def test_square_fp64_full_size_10000(api):
     """n = 10^4 (1e8 DOF), F = g/((1+j)(1+k)) seed 3, FP64 tol 1e-13: whole-matrix parity
     against the oracle run in full on the host cores."""
-    n = 10000
-    F = inputs.square_rhs(n, 3, power=1)
+    F, Xo = _oracle_full(10000, 3, 1)
     X, info = _solve(api, F)
     assert info["J"] == 133
-    Xo = oracle.poisson_square(F, 1e-13)
     assert _relmax(X, Xo) <= TOL_FP64
+
+
+# ------------------------------------------------------------------ FP32 sweeps + FP64 refinement
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 64, 65, 127, 257, 1000])
+def test_square_refine_matches_oracle(api, n):
+    """FP32 residual-propagating sweeps inside FP64 refinement to 1e-10."""
+    F = inputs.square_rhs(n, 300 + n)
+    X, info = _solve(api, F, tol=1e-10, precision="fp32_refine")
+    Xo = oracle.poisson_square(F, 1e-13)
+    assert info["last_residual"] <= 1e-10
+    assert 1 <= info["refine_rounds"] <= 4
+    assert _relmax(X, Xo) <= TOL_REFINE
+
+
+def test_square_refine_manufactured(api):
+    n = 64
+    pc = basis.monomial_coeffs(inputs.poly_values(1), 10)
+    F, Xexact = basis.manufactured_square(pc, n)
+    X, _ = _solve(api, F, tol=1e-12, precision="fp32_refine")
+    assert _relmax(X, Xexact) <= 1e-11
+
+
+def test_square_refine_zero_and_nonfinite(api):
+    n = 40
+    plan = api.plan_create(n, 2, 1e-10, "fp32_refine")
+    Z = torch.zeros(n, n, dtype=torch.float64, device="cuda")
+    X = api.poisson_square_solve(plan, Z)
+    assert torch.count_nonzero(X).item() == 0
+    Fb = torch.from_numpy(inputs.square_rhs(n, 1)).cuda()
+    Fb[3, 4] = float("nan")
+    with pytest.raises(api.FpsError) as e:
+        api.poisson_square_solve(plan, Fb)
+    assert e.value.status == -5
+    api.plan_destroy(plan)
+
+
+def test_square_refine_full_size_4096(api):
+    F, Xo = _oracle_full(4096, 2, 2)
+    X, info = _solve(api, F, tol=1e-10, precision="fp32_refine")
+    assert _relmax(X, Xo) <= TOL_REFINE
+
+
+def test_square_refine_full_size_10000(api):
+    F, Xo = _oracle_full(10000, 3, 1)
+    X, info = _solve(api, F, tol=1e-10, precision="fp32_refine")
+    assert _relmax(X, Xo) <= TOL_REFINE
