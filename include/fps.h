@@ -70,6 +70,7 @@ typedef struct {
     double last_residual;   /* max |R~| / max |F~| after the last FP32_REFINE solve */
     double tol;             /* requested tolerance */
     int64_t device_bytes;   /* device memory owned by the plan */
+    int64_t kernel_launches; /* kernels of this library launched by the last solve */
 } fps_plan_info_t;
 
 /*
@@ -138,6 +139,25 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info);
  * status.  For a batch, the shifts of problem `problem`.
  */
 int fps_plan_shifts(const fps_plan *plan, int64_t problem, double *q, int cap);
+
+/*
+ * fps_plan_set_instrument -- on != 0: record CUDA events around every launch of
+ * the plan's dominant kernel (FP64: the half-step sweep; FP32_REFINE: the column
+ * back-substitution pass), inside the captured graphs, so that its duration can
+ * be read after a solve without changing what runs.  Rebuilds the graphs.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int fps_plan_set_instrument(fps_plan *plan, int on);
+
+/*
+ * fps_plan_kernel_times -- for the last solve of an instrumented plan: number of
+ * timed launches of the dominant kernel (*count), their summed duration in ms
+ * (*total_ms) and the algorithmic bytes they move (*alg_bytes: the arrays each
+ * launch must read and write, 8 bytes per FP64 and 4 per FP32 element; no
+ * scratch, halo or re-read traffic).  Synchronises the plan's stream.
+ * Errors: INVALID_ARG (not instrumented), CUDA.
+ */
+int fps_plan_kernel_times(fps_plan *plan, int *count, double *total_ms, double *alg_bytes);
 
 /* Release every resource of the plan (synchronises its stream).  NULL is a no-op. */
 void fps_plan_destroy(fps_plan *plan);

@@ -72,6 +72,8 @@ def _lib(variant: str = "double") -> ctypes.CDLL:
                                               ctypes.c_int, c_dp, c_dp, c_dp]
             lib.orc_poisson_square.argtypes = [ctypes.c_long, ctypes.c_double, c_dp, c_dp]
             lib.orc_poisson_square.restype = ctypes.c_int
+            lib.orc_poisson_square_partial.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_int, c_dp, c_dp]
+            lib.orc_poisson_square_partial.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_set_num_threads.argtypes = [ctypes.c_int]
             lib.orc_real_bytes.restype = ctypes.c_int
@@ -153,6 +155,15 @@ def poisson_square(F, tol: float = 1e-13, variant: str = "double") -> np.ndarray
     assert F.ndim == 2 and F.shape == (n, n)
     X = np.zeros_like(F)
     _lib(variant).orc_poisson_square(n, tol, _ptr(F), _ptr(X))
+    return X
+
+
+def poisson_square_partial(F, tol: float, jmax: int) -> np.ndarray:
+    """The pipeline of poisson_square stopped after at most jmax ADI iterations."""
+    F = _f64(F)
+    n = F.shape[0]
+    X = np.zeros_like(F)
+    _lib().orc_poisson_square_partial(n, tol, int(jmax), _ptr(F), _ptr(X))
     return X
 
 

@@ -402,7 +402,7 @@ void orc_adi_sylvester(long n, int s, const double *Ad, const double *Ae, const 
 /*   6. X = D_s Y D_s                                            (reading R2)  */
 /* F, X: n x n row-major, X_ij pairs C~_i(y) with C~_j(x).  Returns J.         */
 /* ------------------------------------------------------------------------- */
-static int poisson_square(long n, double tol, const real *F, real *X, double *shifts_q_out)
+static int poisson_square(long n, double tol, const real *F, real *X, double *shifts_q_out, int jmax)
 {
     size_t nn = (size_t)n * (size_t)n;
     long ne = n > 2 ? n - 2 : 1;
@@ -431,7 +431,7 @@ static int poisson_square(long n, double tol, const real *F, real *X, double *sh
         for (int j = 0; j < J; ++j) shifts_q_out[j] = q[j];
 
     band_t A = {n, 2, ad, ae}, B = {n, 2, bd, be};
-    adi_sylvester(&A, &B, Ft, J, pr, qr, Y);
+    adi_sylvester(&A, &B, Ft, (jmax > 0 && jmax < J) ? jmax : J, pr, qr, Y);
 
     for (long i = 0; i < n; ++i)
         for (long k = 0; k < n; ++k) X[i * n + k] = Ds_diag(i) * Y[i * n + k] * Ds_diag(k);
@@ -445,7 +445,22 @@ int orc_poisson_square(long n, double tol, const double *F, double *X)
     size_t nn = (size_t)n * (size_t)n;
     real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
     for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
-    int J = poisson_square(n, tol, Fr, Xr, NULL);
+    int J = poisson_square(n, tol, Fr, Xr, NULL, 0);
+    for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
+    free(Fr);
+    free(Xr);
+    return J;
+}
+
+/* The same pipeline stopped after at most jmax ADI iterations (a bounded sample
+ * of the full solve, used to time the oracle on large problems).  Returns the
+ * full J of (2.9). */
+int orc_poisson_square_partial(long n, double tol, int jmax, const double *F, double *X)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
+    for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
+    int J = poisson_square(n, tol, Fr, Xr, NULL, jmax);
     for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
     free(Fr);
     free(Xr);

@@ -52,6 +52,7 @@ class PlanInfo(ctypes.Structure):
         ("last_residual", ctypes.c_double),
         ("tol", ctypes.c_double),
         ("device_bytes", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
 
@@ -62,6 +63,7 @@ EXPORTED = [
     "fps_plan_create", "fps_plan_create_batched", "fps_plan_set_stream", "fps_poisson_square_solve",
     "fps_poisson_cube_solve", "fps_poisson_adjoint", "fps_plan_info", "fps_plan_shifts", "fps_plan_destroy",
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
+    "fps_plan_set_instrument", "fps_plan_kernel_times",
 ]
 
 
@@ -93,6 +95,8 @@ def lib() -> ctypes.CDLL:
         L.fps_zolotarev_shifts.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
                                                                    dp, ctypes.c_int]
         L.fps_square_bands.argtypes = [i64, dp, dp]
+        L.fps_plan_set_instrument.argtypes = [vp, ctypes.c_int]
+        L.fps_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
         _lib = L
         return L
 
@@ -232,6 +236,19 @@ def plan_shifts(plan: Plan, problem: int = 0) -> np.ndarray:
     q = np.zeros(cap)
     J = _check(lib().fps_plan_shifts(plan.handle, int(problem), _dp(q), cap))
     return q[:J].copy()
+
+
+def plan_set_instrument(plan: Plan, on: bool = True) -> None:
+    _check(lib().fps_plan_set_instrument(plan.handle, 1 if on else 0))
+
+
+def plan_kernel_times(plan: Plan) -> dict:
+    """Dominant-kernel launches of the last solve: count, summed ms, algorithmic bytes."""
+    c = ctypes.c_int()
+    ms = ctypes.c_double()
+    by = ctypes.c_double()
+    _check(lib().fps_plan_kernel_times(plan.handle, ctypes.byref(c), ctypes.byref(ms), ctypes.byref(by)))
+    return {"count": c.value, "total_ms": ms.value, "alg_bytes": by.value}
 
 
 def plan_destroy(plan: Plan) -> None:

@@ -87,6 +87,7 @@ struct fps_plan {
         float *phick = nullptr;     // J x 2 x nchunk
         float4 *segc = nullptr;     // J x 2 x P
         cudaGraphExec_t graph = nullptr;
+        std::vector<cudaEvent_t> ev;  // instrumentation: 2 per iteration around the column back-substitution
     };
     fps::RefineGeometry geo;
     fps::RefineScratch scr;
@@ -97,6 +98,12 @@ struct fps_plan {
     unsigned long long *d_scal = nullptr;   // [0] = max|F~| (scale), [1] = max|R~| (bit patterns)
     unsigned long long *h_scal = nullptr;   // pinned mirror
     int max_rounds = 8;
+
+    // instrumentation and accounting
+    bool instrument = false;
+    std::vector<cudaEvent_t> ev64;          // FP64: 2 per half-step
+    std::vector<int> levels_used;           // FP32_REFINE: levels launched by the last solve
+    int64_t launches_last = 0;
 };
 
 namespace {
@@ -118,7 +125,9 @@ void release(fps_plan *p)
                     p->Y0, p->Y1, p->Pt, p->Ar, p->Cr, p->Dl, p->scr.ck, p->scr.summ, p->d_scal};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (cudaEvent_t e : p->ev64) cudaEventDestroy(e);
     for (auto &L : p->levels) {
+        for (cudaEvent_t e : L.ev) cudaEventDestroy(e);
         if (L.graph) cudaGraphExecDestroy(L.graph);
         if (L.d_q) cudaFree(L.d_q);
         if (L.fac) cudaFree(L.fac);
@@ -148,15 +157,24 @@ cudaError_t enqueue_adi_fp64(fps_plan *p, cudaStream_t st)
         h.G = p->FtT;
         h.Out = p->A;
         h.transposed_out = true;
-        cudaError_t e = fps::launch_halfstep(h, st);
+        const bool ins = p->instrument && (int)p->ev64.size() == 4 * p->J;
+        cudaError_t e;
+        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j], st, cudaEventRecordExternal)) != cudaSuccess) return e;
+        e = fps::launch_halfstep(h, st);
         if (e != cudaSuccess) return e;
+        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j + 1], st, cudaEventRecordExternal)) != cudaSuccess)
+            return e;
         // step 2: (A~ - q) Y^+ = F~ - Y_h (A~ + q); store (Y^+)^T, or Y_J itself last
         h.V = p->A;
         h.G = p->Ft;
         h.Out = p->B;
         h.transposed_out = (j + 1 < p->J);
+        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j + 2], st, cudaEventRecordExternal)) != cudaSuccess)
+            return e;
         e = fps::launch_halfstep(h, st);
         if (e != cudaSuccess) return e;
+        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j + 3], st, cudaEventRecordExternal)) != cudaSuccess)
+            return e;
     }
     return cudaSuccess;
 }
@@ -189,9 +207,10 @@ int build_level_graph(fps_plan *p, fps_plan::Level &L)
         const float *phick = L.phick + (int64_t)j * 2 * p->geo.nchunk;
         const float4 *segc = L.segc + (int64_t)j * 2 * p->geo.P;
         e = fps::launch_row_pass(p->Pt, p->Ar, p->Cr, p->scr, fac, phick, segc, q2, p->n, p->geo, p->cap_stream);
+        const bool ins = p->instrument && (int)L.ev.size() == 2 * L.J;
         if (e == cudaSuccess)
             e = fps::launch_col_pass(p->Cr, p->Ar, p->Dl, p->Pt, p->scr, fac, phick, segc, q2, p->n, p->geo, j == 0,
-                                     p->cap_stream);
+                                     p->cap_stream, ins ? L.ev[2 * j] : nullptr, ins ? L.ev[2 * j + 1] : nullptr);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
@@ -231,6 +250,8 @@ int solve_one_refine(fps_plan *p, const double *F, double *X)
         return FPS_OK;
     }
     FPS_CK(fps::launch_refine_scale_in(F, p->Ft, p->Pt, p->d_s, n, p->ld, p->d_scal, st));
+    p->launches_last += 2;
+    p->levels_used.clear();
     double rel = 1.0;
     double *Ycur = p->Y0, *Ynext = p->Y1;
     bool converged = false;
@@ -242,6 +263,8 @@ int solve_one_refine(fps_plan *p, const double *F, double *X)
         for (size_t l = 0; l < p->levels.size(); ++l)
             if (p->levels[l].tol <= want) li = l;
         FPS_CK(cudaGraphLaunch(p->levels[li].graph, st));
+        p->levels_used.push_back((int)li);
+        p->launches_last += 4LL * p->levels[li].J + 1;
         FPS_CK(cudaMemsetAsync(p->d_scal + 1, 0, sizeof(unsigned long long), st));
         FPS_CK(fps::launch_residual(Ycur, Ynext, p->Dl, p->Ft, p->Pt, p->d_d, p->d_e, p->d_scal, n, p->ld,
                                     p->d_scal + 1, true, round == 0, st));
@@ -260,6 +283,7 @@ int solve_one_refine(fps_plan *p, const double *F, double *X)
     p->refine_rounds = round;
     p->last_residual = rel;
     FPS_CK(fps::launch_scale_out(Ycur, X, p->d_s, n, st));
+    p->launches_last += 1;
     if (!converged) return fail(FPS_ERR_NOT_CONVERGED, "fps_poisson_square_solve: refinement did not reach tol");
     return FPS_OK;
 }
@@ -272,6 +296,7 @@ int solve_one(fps_plan *p, const double *F, double *X)
     FPS_CK(fps::launch_scale_in(F, p->Ft, p->FtT, p->d_s, p->n, st));
     FPS_CK(cudaGraphLaunch(p->graph, st));
     FPS_CK(fps::launch_scale_out(p->B, X, p->d_s, p->n, st));
+    p->launches_last += 2LL * p->J + 2;
     return FPS_OK;
 }
 
@@ -286,6 +311,7 @@ int solve_square(fps_plan *p, const double *F, double *X, const char *what)
     if (f0 < x0 + bytes && x0 < f0 + bytes) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and X overlap");
     DeviceGuard g(p->device);
     const bool fdev = is_device_pointer(F), xdev = is_device_pointer(X);
+    p->launches_last = 0;
     for (int r = 0; r < p->nrhs; ++r) {
         const double *Fr = F + (int64_t)r * nn;
         double *Xr = X + (int64_t)r * nn;
@@ -479,6 +505,83 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->last_residual = plan->last_residual;
     info->tol = plan->tol;
     info->device_bytes = plan->bytes;
+    info->kernel_launches = plan->launches_last;
+    return FPS_OK;
+}
+
+int fps_plan_set_instrument(fps_plan *p, int on)
+{
+    if (!p) return fail(FPS_ERR_INVALID_ARG, "fps_plan_set_instrument: plan is NULL");
+    DeviceGuard g(p->device);
+    FPS_CK(cudaStreamSynchronize(p->cap_stream));
+    if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));
+    else FPS_CK(cudaDeviceSynchronize());
+    p->instrument = on != 0;
+    auto make_events = [&](std::vector<cudaEvent_t> &v, size_t count) -> cudaError_t {
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+        v.clear();
+        if (!p->instrument) return cudaSuccess;
+        v.resize(count);
+        for (auto &e : v) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    };
+    if (p->precision == FPS_FP64) {
+        FPS_CK(make_events(p->ev64, 4 * (size_t)p->J));
+        if (p->graph) cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+        return build_graph(p);
+    }
+    for (auto &L : p->levels) {
+        FPS_CK(make_events(L.ev, 2 * (size_t)L.J));
+        if (L.graph) cudaGraphExecDestroy(L.graph);
+        L.graph = nullptr;
+        int st = build_level_graph(p, L);
+        if (st != FPS_OK) return st;
+    }
+    return FPS_OK;
+}
+
+int fps_plan_kernel_times(fps_plan *p, int *count, double *total_ms, double *alg_bytes)
+{
+    if (!p || !count || !total_ms || !alg_bytes) return fail(FPS_ERR_INVALID_ARG, "fps_plan_kernel_times: NULL argument");
+    if (!p->instrument) return fail(FPS_ERR_INVALID_ARG, "fps_plan_kernel_times: plan is not instrumented");
+    DeviceGuard g(p->device);
+    if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));
+    else FPS_CK(cudaDeviceSynchronize());
+    const double nn = (double)p->n * (double)p->n;
+    int c = 0;
+    double ms = 0.0, bytes = 0.0;
+    if (p->precision == FPS_FP64) {
+        for (int k = 0; k < 2 * p->J; ++k) {
+            float t = 0.f;
+            FPS_CK(cudaEventElapsedTime(&t, p->ev64[2 * k], p->ev64[2 * k + 1]));
+            ms += t;
+            ++c;
+            bytes += (k == 0 ? 2.0 : 3.0) * 8.0 * nn;  // V (unless zero), G read; W written
+        }
+    } else {
+        std::vector<int> seen;
+        for (int li : p->levels_used) {
+            bool dup = false;
+            for (int s2 : seen) dup = dup || s2 == li;
+            if (dup) continue;
+            seen.push_back(li);
+            const auto &L = p->levels[li];
+            for (int j = 0; j < L.J; ++j) {
+                float t = 0.f;
+                FPS_CK(cudaEventElapsedTime(&t, L.ev[2 * j], L.ev[2 * j + 1]));
+                ms += t;
+                ++c;
+                bytes += (j == 0 ? 4.0 : 5.0) * 4.0 * nn;  // c, a (, D) read; rho+, D written
+            }
+        }
+    }
+    *count = c;
+    *total_ms = ms;
+    *alg_bytes = bytes;
     return FPS_OK;
 }
 

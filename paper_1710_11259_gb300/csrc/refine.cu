@@ -620,12 +620,13 @@ cudaError_t launch_row_pass(const float *Pt, float *A, float *C, const RefineScr
 
 cudaError_t launch_col_pass(const float *C, const float *A, float *Dl, float *Pt, const RefineScratch &w,
                             const float4 *fac, const float *phick, const float4 *segc, float q2, int64_t n,
-                            const RefineGeometry &g, bool first, cudaStream_t st)
+                            const RefineGeometry &g, bool first, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     const dim3 grid((unsigned)g.nblk, (unsigned)g.P), block(64);
     fwd_local_kernel<2, kDF><<<grid, block, 0, st>>>(C, A, w.ck, w.summ, fac, (int)n, (int)g.ld, (int)g.Ls);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ev0 && (e = cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (first)
         col_bwd_kernel<kDB, true><<<grid, block, colb_smem<kDB>(), st>>>(C, A, Dl, Pt, w.ck, w.summ, fac, phick, segc,
                                                                         q2, (int)n, (int)g.ld, (int)g.Ls, (int)g.P,
@@ -634,7 +635,9 @@ cudaError_t launch_col_pass(const float *C, const float *A, float *Dl, float *Pt
         col_bwd_kernel<kDB, false><<<grid, block, colb_smem<kDB>(), st>>>(C, A, Dl, Pt, w.ck, w.summ, fac, phick,
                                                                          segc, q2, (int)n, (int)g.ld, (int)g.Ls,
                                                                          (int)g.P, (int)g.nchunk);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev1) e = cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
+    return e;
 }
 
 cudaError_t launch_residual(const double *Y, double *Yout, const float *Dl, const double *Ft, float *Pt, const double *d,

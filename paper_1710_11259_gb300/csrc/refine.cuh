@@ -34,9 +34,11 @@ cudaError_t launch_row_pass(const float *Pt, float *A, float *C, const RefineScr
                             cudaStream_t st);
 
 // Column pass: Pt = (C + 2q (L-q)^{-1} C)^T, Dl -= 2q (L-q)^{-1} A (Dl = -2q (L-q)^{-1} A when first).
+// If ev0/ev1 are given they are recorded around the back-substitution kernel (timing).
 cudaError_t launch_col_pass(const float *C, const float *A, float *Dl, float *Pt, const RefineScratch &w,
                             const float4 *fac, const float *phick, const float4 *segc, float q2, int64_t n,
-                            const RefineGeometry &g, bool first, cudaStream_t st);
+                            const RefineGeometry &g, bool first, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                            cudaEvent_t ev1 = nullptr);
 
 // Yout = Y + s Dl (if apply_update; Y read as zero if y_zero), R = F~ - A~ Yout - Yout A~,
 // Pt = (R/s)^T, rmax = max |R| (bit pattern).  s is read from device memory (bit pattern).
