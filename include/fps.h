@@ -159,6 +159,28 @@ int fps_plan_set_instrument(fps_plan *plan, int on);
  */
 int fps_plan_kernel_times(fps_plan *plan, int *count, double *total_ms, double *alg_bytes);
 
+/*
+ * fps_poisson_square_solve_noalloc -- the FP64 square solve of fps_poisson_square_solve
+ * (same shifts, iteration count and kernels) for n <= 256, without allocating
+ * anything.  The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they solve (a caching allocator that owns the
+ * device memory, hosts that forbid allocation after start-up, code that must avoid
+ * the synchronisation cudaMalloc/cudaFree can cause).  No plan is needed.
+ *   n       1 <= n <= 256;  tol in (0, 1) with J of (2.9) at most 256.
+ *   F, X    device pointers (the caller allocates them), n x n row-major FP64,
+ *           not overlapping; F is not modified.
+ *   stream  cudaStream_t the work is enqueued on (asynchronous; NULL = legacy stream).
+ * Work arrays live in one fixed 4 MiB device array inside the library that every
+ * GPU loading the library holds until the process exits.  The first call on a
+ * device looks its address up (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  All calls on a device share the
+ * array, which keeps the last call's contents (each call rewrites everything it
+ * reads); calls that overlap on the GPU race on it, so order them on one stream.
+ * Errors (status code only; fps_last_error is not updated): INVALID_ARG (n or tol
+ * out of range, NULL/overlapping/non-device F or X), CUDA.
+ */
+int fps_poisson_square_solve_noalloc(int64_t n, double tol, const double *F, double *X, void *stream);
+
 /* Release every resource of the plan (synchronises its stream).  NULL is a no-op. */
 void fps_plan_destroy(fps_plan *plan);
 

@@ -63,7 +63,7 @@ EXPORTED = [
     "fps_plan_create", "fps_plan_create_batched", "fps_plan_set_stream", "fps_poisson_square_solve",
     "fps_poisson_cube_solve", "fps_poisson_adjoint", "fps_plan_info", "fps_plan_shifts", "fps_plan_destroy",
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
-    "fps_plan_set_instrument", "fps_plan_kernel_times",
+    "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
 ]
 
 
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.fps_square_bands.argtypes = [i64, dp, dp]
         L.fps_plan_set_instrument.argtypes = [vp, ctypes.c_int]
         L.fps_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
+        L.fps_poisson_square_solve_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp]
         _lib = L
         return L
 
@@ -255,6 +256,14 @@ def plan_destroy(plan: Plan) -> None:
     if plan._h:
         lib().fps_plan_destroy(plan._h)
         plan._h = ctypes.c_void_p()
+
+
+def poisson_square_solve_noalloc(F, X, tol: float = 1e-13, stream: Optional[int] = None) -> int:
+    """FP64 square solve for n <= 256 that allocates nothing (see fps.h); F and X are
+    caller-allocated CUDA tensors.  Returns the status code (0 = ok)."""
+    s = _current_stream() if stream is None else int(stream)
+    return int(lib().fps_poisson_square_solve_noalloc(int(F.shape[-1]), float(tol), ctypes.c_void_p(_ptr(F)),
+                                                      ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(s)))
 
 
 def zolotarev_shifts(a: float, b: float, c: float, d: float, tol: float, J: int = 0):

@@ -144,4 +144,35 @@ void zolotarev_shifts(double a, double b, double c, double d, int J, std::vector
     }
 }
 
+// Allocation-free forms of square_bands / inv_sqrt_E / zolotarev_shifts_symmetric
+// (caller-provided arrays; same arithmetic), for the entry point that must not
+// allocate.
+void square_bands_into(int64_t n, double *d, double *e, double *s)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double x = (double)j;
+        double Ej = (x + 1.0) * (x + 2.0);
+        double Mjj = 2.0 * (x + 1.0) * (x + 2.0) / ((2.0 * x + 1.0) * (2.0 * x + 5.0));
+        d[j] = -Mjj / Ej;
+        e[j] = 0.0;
+        if (j + 2 < n) {
+            double Ej2 = (x + 3.0) * (x + 4.0);
+            double prod4 = (x + 1.0) * (x + 2.0) * (x + 3.0) * (x + 4.0);
+            double Mj2 = -std::sqrt(prod4 * (2.0 * x + 3.0) / (2.0 * x + 7.0)) / ((2.0 * x + 3.0) * (2.0 * x + 5.0));
+            e[j] = -Mj2 / std::sqrt(Ej * Ej2);
+        }
+        s[j] = 1.0 / std::sqrt(((double)j + 1.0) * ((double)j + 2.0));
+    }
+}
+
+void zolotarev_shifts_symmetric_into(double lo, double hi, int J, double *q)
+{
+    const double kp = lo / hi;
+    const double K = ellip_K_kp(kp);
+    for (int j = 0; 2 * j + 1 <= J; ++j) q[j] = dn_lower_half((2.0 * j + 1.0) * K / (2.0 * J), kp);
+    for (int j = 0; j < J; ++j)
+        if (2 * j + 1 > J) q[j] = kp / q[J - 1 - j];
+    for (int j = 0; j < J; ++j) q[j] = hi * q[j];
+}
+
 }  // namespace fps
