@@ -1,0 +1,29 @@
+"""torch.autograd wrapper of the square solve.
+
+The solve map F -> X of (3.6) is linear and self-adjoint in the Frobenius inner
+product (it is a rational function of the commuting symmetric operators
+Y -> A~ Y and Y -> Y A~, wrapped by the diagonal scalings of (3.9)), so the
+backward pass is the same solve applied to dL/dX through ``fps_poisson_adjoint``.
+The forward pass saves nothing but the plan handle.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+class PoissonSquareFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, F: torch.Tensor, plan: api.Plan) -> torch.Tensor:
+        ctx.plan = plan
+        return api.poisson_square_solve(plan, F.contiguous())
+
+    @staticmethod
+    def backward(ctx, gX: torch.Tensor):
+        return api.poisson_adjoint(ctx.plan, gX.contiguous()), None
+
+
+def poisson_square(F: torch.Tensor, plan: api.Plan) -> torch.Tensor:
+    """Differentiable X = solve(F) on the plan's device (CUDA float64 tensors)."""
+    return PoissonSquareFn.apply(F, plan)
