@@ -10,7 +10,7 @@
 #include "../../include/fps.h"
 #include "host_math.h"
 #include "kernels.cuh"
-#include "refine.cuh"
+#include "refine_engine.h"
 
 namespace {
 
@@ -77,32 +77,15 @@ struct fps_plan {
     int refine_rounds = 0;
     double last_residual = 0;
 
-    // FPS_FP32_REFINE: FP32 inner ADI (residual-propagating form) per tolerance level
-    struct Level {
-        double tol = 0;
-        int J = 0;
-        std::vector<double> q;
-        double *d_q = nullptr;
-        float4 *fac = nullptr;      // J x n
-        float *phick = nullptr;     // J x 2 x nchunk
-        float4 *segc = nullptr;     // J x 2 x P
-        cudaGraphExec_t graph = nullptr;
-        std::vector<cudaEvent_t> ev;  // instrumentation: 2 per iteration around the column back-substitution
-    };
-    fps::RefineGeometry geo;
-    fps::RefineScratch scr;
-    std::vector<Level> levels;
-    int64_t ld = 0;                    // padded leading dimension of the FP32 arrays
-    double *Y0 = nullptr, *Y1 = nullptr;
-    float *Pt = nullptr, *Ar = nullptr, *Cr = nullptr, *Dl = nullptr;
-    unsigned long long *d_scal = nullptr;   // [0] = max|F~| (scale), [1] = max|R~| (bit patterns)
-    unsigned long long *h_scal = nullptr;   // pinned mirror
-    int max_rounds = 8;
+    // FPS_FP32_REFINE (single problem or batch): the refinement engine
+    fps::RefineEngine *eng = nullptr;
+    std::vector<int64_t> batch_ns;   // sizes of a batched plan (empty otherwise)
+    int64_t total_elems = 0;         // doubles in F (and X) for all right-hand sides / problems
+    double *stage_in = nullptr, *stage_out = nullptr;  // lazily allocated for host pointers
 
-    // instrumentation and accounting
+    // instrumentation and accounting (FP64 path)
     bool instrument = false;
     std::vector<cudaEvent_t> ev64;          // FP64: 2 per half-step
-    std::vector<int> levels_used;           // FP32_REFINE: levels launched by the last solve
     int64_t launches_last = 0;
 };
 
@@ -121,20 +104,15 @@ void release(fps_plan *p)
     if (!p) return;
     DeviceGuard g(p->device);
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    void *bufs[] = {p->d_d, p->d_e, p->d_s, p->d_q, p->d_fac, p->Ft, p->FtT, p->A, p->B, p->Z,
-                    p->Y0, p->Y1, p->Pt, p->Ar, p->Cr, p->Dl, p->scr.ck, p->scr.summ, p->d_scal};
+    void *bufs[] = {p->d_d, p->d_e, p->d_s, p->d_q, p->d_fac, p->Ft, p->FtT, p->A, p->B, p->Z, p->stage_in,
+                    p->stage_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev64) cudaEventDestroy(e);
-    for (auto &L : p->levels) {
-        for (cudaEvent_t e : L.ev) cudaEventDestroy(e);
-        if (L.graph) cudaGraphExecDestroy(L.graph);
-        if (L.d_q) cudaFree(L.d_q);
-        if (L.fac) cudaFree(L.fac);
-        if (L.phick) cudaFree(L.phick);
-        if (L.segc) cudaFree(L.segc);
+    if (p->eng) {
+        p->eng->release();
+        delete p->eng;
     }
-    if (p->h_scal) cudaFreeHost(p->h_scal);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
 }
@@ -196,102 +174,9 @@ int build_graph(fps_plan *p)
     return FPS_OK;
 }
 
-// Capture the inner ADI of one tolerance level: J x (row pass, column pass).
-int build_level_graph(fps_plan *p, fps_plan::Level &L)
-{
-    FPS_CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int j = 0; j < L.J && e == cudaSuccess; ++j) {
-        const float q2 = (float)(2.0 * L.q[j]);
-        const float4 *fac = L.fac + (int64_t)j * p->n;
-        const float *phick = L.phick + (int64_t)j * 2 * p->geo.nchunk;
-        const float4 *segc = L.segc + (int64_t)j * 2 * p->geo.P;
-        e = fps::launch_row_pass(p->Pt, p->Ar, p->Cr, p->scr, fac, phick, segc, q2, p->n, p->geo, p->cap_stream);
-        const bool ins = p->instrument && (int)L.ev.size() == 2 * L.J;
-        if (e == cudaSuccess)
-            e = fps::launch_col_pass(p->Cr, p->Ar, p->Dl, p->Pt, p->scr, fac, phick, segc, q2, p->n, p->geo, j == 0,
-                                     p->cap_stream, ins ? L.ev[2 * j] : nullptr, ins ? L.ev[2 * j + 1] : nullptr);
-    }
-    cudaGraph_t g = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
-    if (e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return fail(FPS_ERR_CUDA, std::string("refine graph capture: ") + cudaGetErrorString(e));
-    }
-    FPS_CK(e2);
-    e = cudaGraphInstantiate(&L.graph, g, 0);
-    cudaGraphDestroy(g);
-    FPS_CK(e);
-    return FPS_OK;
-}
-
-double bits_to_double(unsigned long long b)
-{
-    double d;
-    std::memcpy(&d, &b, sizeof(d));
-    return d;
-}
-
-// FP32 sweeps + FP64 refinement for one right-hand side (device pointers).
-int solve_one_refine(fps_plan *p, const double *F, double *X)
-{
-    cudaStream_t st = p->stream;
-    const int64_t n = p->n;
-    FPS_CK(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(unsigned long long), st));
-    FPS_CK(fps::launch_absmax_scaled(F, p->d_s, n, p->d_scal, st));
-    FPS_CK(cudaMemcpyAsync(p->h_scal, p->d_scal, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    FPS_CK(cudaStreamSynchronize(st));
-    const double sF = bits_to_double(p->h_scal[0]);
-    if (!std::isfinite(sF)) return fail(FPS_ERR_NONFINITE, "fps_poisson_square_solve: F holds NaN or Inf");
-    if (sF == 0.0) {
-        FPS_CK(cudaMemsetAsync(X, 0, sizeof(double) * n * n, st));
-        p->refine_rounds = 0;
-        p->last_residual = 0.0;
-        return FPS_OK;
-    }
-    FPS_CK(fps::launch_refine_scale_in(F, p->Ft, p->Pt, p->d_s, n, p->ld, p->d_scal, st));
-    p->launches_last += 2;
-    p->levels_used.clear();
-    double rel = 1.0;
-    double *Ycur = p->Y0, *Ynext = p->Y1;
-    bool converged = false;
-    int round = 0;
-    for (; round < p->max_rounds; ++round) {
-        // inner tolerance: aim one decade below what this round must gain
-        const double want = 0.1 * p->tol / rel;
-        size_t li = 0;
-        for (size_t l = 0; l < p->levels.size(); ++l)
-            if (p->levels[l].tol <= want) li = l;
-        FPS_CK(cudaGraphLaunch(p->levels[li].graph, st));
-        p->levels_used.push_back((int)li);
-        p->launches_last += 4LL * p->levels[li].J + 1;
-        FPS_CK(cudaMemsetAsync(p->d_scal + 1, 0, sizeof(unsigned long long), st));
-        FPS_CK(fps::launch_residual(Ycur, Ynext, p->Dl, p->Ft, p->Pt, p->d_d, p->d_e, p->d_scal, n, p->ld,
-                                    p->d_scal + 1, true, round == 0, st));
-        FPS_CK(cudaMemcpyAsync(p->h_scal + 1, p->d_scal + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        FPS_CK(cudaStreamSynchronize(st));
-        std::swap(Ycur, Ynext);
-        const double r = bits_to_double(p->h_scal[1]) / sF;
-        if (!std::isfinite(r)) return fail(FPS_ERR_NONFINITE, "fps_poisson_square_solve: non-finite residual");
-        rel = r;
-        if (rel <= p->tol) {
-            converged = true;
-            ++round;
-            break;
-        }
-    }
-    p->refine_rounds = round;
-    p->last_residual = rel;
-    FPS_CK(fps::launch_scale_out(Ycur, X, p->d_s, n, st));
-    p->launches_last += 1;
-    if (!converged) return fail(FPS_ERR_NOT_CONVERGED, "fps_poisson_square_solve: refinement did not reach tol");
-    return FPS_OK;
-}
-
-// One right-hand side, device pointers.
+// One right-hand side, device pointers (FP64 path).
 int solve_one(fps_plan *p, const double *F, double *X)
 {
-    if (p->precision == FPS_FP32_REFINE) return solve_one_refine(p, F, X);
     cudaStream_t st = p->stream;
     FPS_CK(fps::launch_scale_in(F, p->Ft, p->FtT, p->d_s, p->n, st));
     FPS_CK(cudaGraphLaunch(p->graph, st));
@@ -300,37 +185,61 @@ int solve_one(fps_plan *p, const double *F, double *X)
     return FPS_OK;
 }
 
+// FP32_REFINE (single or batched): the whole packed F at once.
+int solve_engine(fps_plan *p, const double *F, double *X, bool fdev, bool xdev, const char *what)
+{
+    const size_t bytes = sizeof(double) * (size_t)p->total_elems;
+    const double *Fd = F;
+    double *Xd = X;
+    if (!fdev) {
+        if (!p->stage_in) FPS_CK(cudaMalloc((void **)&p->stage_in, bytes));
+        FPS_CK(cudaMemcpyAsync(p->stage_in, F, bytes, cudaMemcpyHostToDevice, p->stream));
+        Fd = p->stage_in;
+    }
+    if (!xdev) {
+        if (!p->stage_out) FPS_CK(cudaMalloc((void **)&p->stage_out, bytes));
+        Xd = p->stage_out;
+    }
+    std::string err;
+    const int st = p->eng->solve(Fd, Xd, p->stream, err);
+    if (st != FPS_OK && st != FPS_ERR_NOT_CONVERGED) return fail(st, std::string(what) + ": " + err);
+    p->launches_last = p->eng->launches_last;
+    if (!xdev) {
+        FPS_CK(cudaMemcpyAsync(X, Xd, bytes, cudaMemcpyDeviceToHost, p->stream));
+        FPS_CK(cudaStreamSynchronize(p->stream));
+    }
+    if (st != FPS_OK) return fail(st, std::string(what) + ": " + err);
+    return FPS_OK;
+}
+
 int solve_square(fps_plan *p, const double *F, double *X, const char *what)
 {
     if (!p) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": plan is NULL");
     if (p->dim != 2) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": plan is not two-dimensional");
     if (!F || !X) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": NULL F or X");
-    const int64_t nn = p->n * p->n;
-    const size_t bytes = sizeof(double) * (size_t)nn * (size_t)p->nrhs;
+    const size_t bytes = sizeof(double) * (size_t)p->total_elems;
     const char *f0 = (const char *)F, *x0 = (const char *)X;
     if (f0 < x0 + bytes && x0 < f0 + bytes) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and X overlap");
     DeviceGuard g(p->device);
     const bool fdev = is_device_pointer(F), xdev = is_device_pointer(X);
     p->launches_last = 0;
+    if (p->eng) return solve_engine(p, F, X, fdev, xdev, what);
+    const int64_t nn = p->n * p->n;
     for (int r = 0; r < p->nrhs; ++r) {
         const double *Fr = F + (int64_t)r * nn;
         double *Xr = X + (int64_t)r * nn;
-        const bool refine = p->precision == FPS_FP32_REFINE;
-        double *stage_in = refine ? p->Y1 : p->B;   // free until the solve overwrites it
-        double *stage_out = refine ? p->Ft : p->A;  // free once the solve has finished with it
         const double *Fd = Fr;
         if (!fdev) {
-            FPS_CK(cudaMemcpyAsync(stage_in, Fr, sizeof(double) * nn, cudaMemcpyHostToDevice, p->stream));
-            Fd = stage_in;
+            FPS_CK(cudaMemcpyAsync(p->B, Fr, sizeof(double) * nn, cudaMemcpyHostToDevice, p->stream));
+            Fd = p->B;
         }
-        double *Xd = xdev ? Xr : stage_out;
+        double *Xd = xdev ? Xr : p->A;
         int s = solve_one(p, Fd, Xd);
-        if (s != FPS_OK && s != FPS_ERR_NOT_CONVERGED) return s;
+        if (s != FPS_OK) return s;
         if (!xdev) {
-            FPS_CK(cudaMemcpyAsync(Xr, stage_out, sizeof(double) * nn, cudaMemcpyDeviceToHost, p->stream));
+            FPS_CK(cudaMemcpyAsync(Xr, p->A, sizeof(double) * nn, cudaMemcpyDeviceToHost, p->stream));
             FPS_CK(cudaStreamSynchronize(p->stream));
         }
-        if (s != FPS_OK) return s;
     }
     if (!fdev && xdev) FPS_CK(cudaStreamSynchronize(p->stream));  // host F must stay valid only until copied
     FPS_CK(cudaGetLastError());
@@ -360,6 +269,7 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     p->precision = precision;
     p->nrhs = nrhs;
     p->stream = (cudaStream_t)stream;
+    p->total_elems = n * n * nrhs;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
         return fail(FPS_ERR_CUDA, "fps_plan_create: no CUDA device");
@@ -389,8 +299,8 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     PCK(dmalloc(p, &p->d_e, n));
     PCK(dmalloc(p, &p->d_s, n));
     PCK(dmalloc(p, &p->d_q, p->J));
-    PCK(dmalloc(p, &p->Ft, nn));
     if (precision == FPS_FP64) {
+        PCK(dmalloc(p, &p->Ft, nn));
         PCK(dmalloc(p, &p->d_fac, (size_t)p->J * n));
         PCK(dmalloc(p, &p->FtT, nn));
         PCK(dmalloc(p, &p->A, nn));
@@ -407,48 +317,14 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
         int st = build_graph(p);
         if (st != FPS_OK) return bail(st);
     } else {
-        // FP32 arrays with a leading dimension padded to 32 (128-byte rows for cp.async).
         if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: FP32_REFINE supports n <= 40000"));
-        int sms = 0;
-        PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-        p->geo = fps::refine_geometry(n, sms);
-        p->ld = p->geo.ld;
-        const size_t nl = (size_t)n * (size_t)p->ld;
-        PCK(dmalloc(p, &p->Y0, nn));
-        PCK(dmalloc(p, &p->Y1, nn));
-        PCK(dmalloc(p, &p->Pt, nl));
-        PCK(dmalloc(p, &p->Ar, nl));
-        PCK(dmalloc(p, &p->Cr, nl));
-        PCK(dmalloc(p, &p->Dl, nl));
-        PCK(dmalloc(p, &p->scr.ck, (size_t)fps::refine_checkpoint_floats(p->geo)));
-        PCK(dmalloc(p, &p->scr.summ, (size_t)fps::refine_summary_float2(p->geo)));
-        PCK(dmalloc(p, &p->d_scal, 2));
-        PCK(cudaMallocHost((void **)&p->h_scal, 2 * sizeof(unsigned long long)));
-        float *zero_bufs[] = {p->Pt, p->Ar, p->Cr, p->Dl};
-        for (float *b : zero_bufs) PCK(cudaMemsetAsync(b, 0, sizeof(float) * nl, p->cap_stream));
-        PCK(fps::refine_setup_kernels());
-        // inner tolerance levels, finest (FP32-limited) first
-        const double level_tols[] = {1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2};
-        for (double lt : level_tols) {
-            fps_plan::Level L;
-            L.tol = lt;
-            L.J = fps::adi_iterations(-1.0, -eps, eps, 1.0, lt);
-            fps::zolotarev_shifts_symmetric(eps, 1.0, L.J, L.q);
-            p->levels.push_back(L);
-        }
-        for (auto &L : p->levels) {
-            PCK(dmalloc(p, &L.d_q, L.J));
-            PCK(dmalloc(p, &L.fac, (size_t)L.J * n));
-            PCK(dmalloc(p, &L.phick, (size_t)L.J * 2 * p->geo.nchunk));
-            PCK(dmalloc(p, &L.segc, (size_t)L.J * 2 * p->geo.P));
-            PCK(cudaMemcpyAsync(L.d_q, L.q.data(), sizeof(double) * L.J, cudaMemcpyHostToDevice, p->cap_stream));
-            PCK(fps::launch_factors32(p->d_d, p->d_e, L.d_q, L.J, n, p->geo, L.fac, L.phick, L.segc, p->cap_stream));
-        }
+        if (nrhs > 256) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: FP32_REFINE supports nrhs <= 256"));
         PCK(cudaStreamSynchronize(p->cap_stream));
-        for (auto &L : p->levels) {
-            int st = build_level_graph(p, L);
-            if (st != FPS_OK) return bail(st);
-        }
+        p->eng = new fps::RefineEngine();
+        std::string err;
+        const int st = p->eng->create(std::vector<int64_t>{n}, nrhs, tol, p->cap_stream, 0, err);
+        if (st != FPS_OK) return bail(fail(st, "fps_plan_create: " + err));
+        p->bytes += p->eng->bytes;
     }
 #undef PCK
     *out = p;
@@ -458,9 +334,47 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
 int fps_plan_create_batched(fps_plan **out, const int64_t *ns, int64_t count, int nrhs, double tol, int precision,
                             void *stream)
 {
-    (void)ns; (void)count; (void)nrhs; (void)tol; (void)precision; (void)stream;
-    if (out) *out = nullptr;
-    return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create_batched: not built yet");
+    if (!out) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_batched: out is NULL");
+    *out = nullptr;
+    if (!ns || count < 1) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_batched: need count >= 1 sizes");
+    if (nrhs < 1 || nrhs > 256) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_batched: nrhs must be in [1, 256]");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_batched: tol must lie in (0, 1)");
+    if (precision != FPS_FP32_REFINE)
+        return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create_batched: batches run in FPS_FP32_REFINE");
+    std::vector<int64_t> v(ns, ns + count);
+    int64_t nmax = 0, total = 0;
+    for (int64_t n : v) {
+        if (n < 1 || n > 40000) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_batched: every n must be in [1, 40000]");
+        nmax = n > nmax ? n : nmax;
+        total += n * n * nrhs;
+    }
+    fps_plan *p = new fps_plan();
+    p->n = nmax;
+    p->dim = 2;
+    p->tol = tol;
+    p->precision = precision;
+    p->nrhs = nrhs;
+    p->stream = (cudaStream_t)stream;
+    p->batch_ns = v;
+    p->total_elems = total;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return fail(FPS_ERR_CUDA, "fps_plan_create_batched: no CUDA device");
+    }
+    if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete p;
+        return fail(FPS_ERR_CUDA, "fps_plan_create_batched: stream creation failed");
+    }
+    p->eng = new fps::RefineEngine();
+    std::string err;
+    const int st = p->eng->create(v, nrhs, tol, p->cap_stream, 0, err);
+    if (st != FPS_OK) {
+        release(p);
+        return fail(st, "fps_plan_create_batched: " + err);
+    }
+    p->bytes += p->eng->bytes;
+    *out = p;
+    return FPS_OK;
 }
 
 int fps_plan_set_stream(fps_plan *plan, void *stream)
@@ -498,11 +412,11 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->dim = plan->dim;
     info->precision = plan->precision;
     info->nrhs = plan->nrhs;
-    info->batch = 1;
+    info->batch = plan->batch_ns.empty() ? 1 : (int64_t)plan->batch_ns.size();
     info->J = plan->J;
-    info->J_inner = plan->levels.empty() ? 0 : plan->levels[0].J;
-    info->refine_rounds = plan->refine_rounds;
-    info->last_residual = plan->last_residual;
+    info->J_inner = plan->eng ? plan->eng->J_inner_first : 0;
+    info->refine_rounds = plan->eng ? plan->eng->rounds_last : 0;
+    info->last_residual = plan->eng ? plan->eng->resid_last : 0.0;
     info->tol = plan->tol;
     info->device_bytes = plan->bytes;
     info->kernel_launches = plan->launches_last;
@@ -517,31 +431,20 @@ int fps_plan_set_instrument(fps_plan *p, int on)
     if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));
     else FPS_CK(cudaDeviceSynchronize());
     p->instrument = on != 0;
-    auto make_events = [&](std::vector<cudaEvent_t> &v, size_t count) -> cudaError_t {
-        for (cudaEvent_t e : v) cudaEventDestroy(e);
-        v.clear();
-        if (!p->instrument) return cudaSuccess;
-        v.resize(count);
-        for (auto &e : v) {
-            cudaError_t r = cudaEventCreate(&e);
-            if (r != cudaSuccess) return r;
-        }
-        return cudaSuccess;
-    };
-    if (p->precision == FPS_FP64) {
-        FPS_CK(make_events(p->ev64, 4 * (size_t)p->J));
-        if (p->graph) cudaGraphExecDestroy(p->graph);
-        p->graph = nullptr;
-        return build_graph(p);
+    if (p->eng) {
+        std::string err;
+        const int st = p->eng->set_instrument(p->instrument, err);
+        return st == FPS_OK ? FPS_OK : fail(st, "fps_plan_set_instrument: " + err);
     }
-    for (auto &L : p->levels) {
-        FPS_CK(make_events(L.ev, 2 * (size_t)L.J));
-        if (L.graph) cudaGraphExecDestroy(L.graph);
-        L.graph = nullptr;
-        int st = build_level_graph(p, L);
-        if (st != FPS_OK) return st;
+    for (cudaEvent_t e : p->ev64) cudaEventDestroy(e);
+    p->ev64.clear();
+    if (p->instrument) {
+        p->ev64.resize(4 * (size_t)p->J);
+        for (auto &e : p->ev64) FPS_CK(cudaEventCreate(&e));
     }
-    return FPS_OK;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+    return build_graph(p);
 }
 
 int fps_plan_kernel_times(fps_plan *p, int *count, double *total_ms, double *alg_bytes)
@@ -551,33 +454,20 @@ int fps_plan_kernel_times(fps_plan *p, int *count, double *total_ms, double *alg
     DeviceGuard g(p->device);
     if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));
     else FPS_CK(cudaDeviceSynchronize());
+    if (p->eng) {
+        std::string err;
+        const int st = p->eng->kernel_times(count, total_ms, alg_bytes, err);
+        return st == FPS_OK ? FPS_OK : fail(st, "fps_plan_kernel_times: " + err);
+    }
     const double nn = (double)p->n * (double)p->n;
     int c = 0;
     double ms = 0.0, bytes = 0.0;
-    if (p->precision == FPS_FP64) {
-        for (int k = 0; k < 2 * p->J; ++k) {
-            float t = 0.f;
-            FPS_CK(cudaEventElapsedTime(&t, p->ev64[2 * k], p->ev64[2 * k + 1]));
-            ms += t;
-            ++c;
-            bytes += (k == 0 ? 2.0 : 3.0) * 8.0 * nn;  // V (unless zero), G read; W written
-        }
-    } else {
-        std::vector<int> seen;
-        for (int li : p->levels_used) {
-            bool dup = false;
-            for (int s2 : seen) dup = dup || s2 == li;
-            if (dup) continue;
-            seen.push_back(li);
-            const auto &L = p->levels[li];
-            for (int j = 0; j < L.J; ++j) {
-                float t = 0.f;
-                FPS_CK(cudaEventElapsedTime(&t, L.ev[2 * j], L.ev[2 * j + 1]));
-                ms += t;
-                ++c;
-                bytes += (j == 0 ? 4.0 : 5.0) * 4.0 * nn;  // c, a (, D) read; rho+, D written
-            }
-        }
+    for (int k = 0; k < 2 * p->J; ++k) {
+        float t = 0.f;
+        FPS_CK(cudaEventElapsedTime(&t, p->ev64[2 * k], p->ev64[2 * k + 1]));
+        ms += t;
+        ++c;
+        bytes += (k == 0 ? 2.0 : 3.0) * 8.0 * nn;  // V (unless zero), G read; W written
     }
     *count = c;
     *total_ms = ms;

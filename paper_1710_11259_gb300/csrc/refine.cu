@@ -1,4 +1,5 @@
-// FP32 sweeps inside an FP64 iterative refinement (precision FPS_FP32_REFINE).
+// FP32 sweeps inside an FP64 iterative refinement (precision FPS_FP32_REFINE),
+// for one problem or a batch of problems of different sizes.
 //
 // The refinement solves A~ D + D A~ = R~ for the correction D of the current
 // FP64 iterate Y, with R~ = F~ - A~ Y - Y A~ computed in FP64.  The inner solve
@@ -11,15 +12,28 @@
 // The second form never multiplies the (large) iterate by A~: every quantity
 // fed back into a solve is the residual, whose propagation factors are bounded
 // by one.  In FP32 it keeps the accuracy the first form loses to cancellation
-// at small shifts.  One iteration is two kernels:
-//   row pass   a = (R - q)^{-1} rho,   c = rho + 2q a            [(R+q)(R-q)^{-1} rho]
+// at small shifts.  One iteration is two passes:
+//   row pass    a = (R - q)^{-1} rho,   c = rho + 2q a            [(R+q)(R-q)^{-1} rho]
 //   column pass g = (L - q)^{-1} c,  b = (L - q)^{-1} a,
 //               rho+ = c + 2q g,  D <- D - 2q b
 // Both are column solves (the row pass runs on rho^T), one thread per (column,
 // row parity), Thomas elimination on the even/odd decoupled A~ - q I (App. B).
-// Instead of spilling the forward elimination, each thread checkpoints it every
-// kChunk rows and recomputes chunk by chunk in reverse, so every matrix is read
-// twice and written once (no n x n scratch traffic).
+//
+// Work decomposition.  Each (column, parity) system of m rows is cut into P
+// segments of Ls rows; a CTA (two warps, one per parity) owns 32 columns of one
+// segment of one right-hand side of one problem.  With the true forward value
+// z_in entering a segment and the true back-substitution value x_out leaving it,
+//     z_t = zl_t + Phi_t z_in                 (zl: forward sweep started from 0)
+//     x_start = a + B z_in + Psi x_out,        a = sum_t kappa_t zl_t
+// where Phi_t = prod(-lf), kappa_t = ip_t prod_{u<t}(-uf_u), Psi = prod(-uf),
+// B = sum kappa_t Phi_t depend only on the shift (precomputed per shift in FP64).
+// Pass kernel 1 runs the local forward sweeps, checkpoints zl every kChunk rows
+// and writes (zl_end, a) per segment; pass kernel 2 chains the segments (O(P) per
+// warp, in registers), recomputes each chunk from its checkpoint (converted to the
+// true z) in reverse order and back-substitutes.  Every input is read twice and
+// every output written once; no n x n scratch.  A work-item table lists the CTAs
+// of all problems, so one launch sweeps a whole batch; problems that have finished
+// their iterations (or are inactive) exit at once.
 #include <cuda_runtime.h>
 
 #include "refine.cuh"
@@ -28,9 +42,11 @@ namespace fps {
 
 namespace {
 
-constexpr int kRC = 32;       // columns per CTA
-constexpr int kChunk = 32;    // rows per checkpoint chunk (per parity)
-constexpr int kTileRows = 64; // rows of a transposed-store tile (both parities)
+constexpr int kRC = 32;        // columns per CTA
+constexpr int kChunk = 32;     // rows per checkpoint chunk (per parity)
+constexpr int kTileRows = 64;  // rows of a transposed-store tile (both parities)
+constexpr int kU = 4;          // rows per shared-memory slot
+constexpr int kMaxSeg = 64;    // segments per (column, parity) system
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -45,25 +61,45 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Rows move through shared memory in slots of kU consecutive rows of one
-// parity; a warp waits once per slot.
-constexpr int kU = 4;         // rows per slot
-constexpr int kMaxSeg = 32;   // segments per (column, parity) system
+// Per-CTA view of one work item.
+struct ItemView {
+    int n, ld, Ls, P, nchunk, seg, k0;
+    const float4 *fac;
+    const float *phick;
+    const float4 *segc;
+    float q2;
+    int64_t off;   // FP32 element offset of this problem / right-hand side
+    float *ck;     // checkpoints of this problem / right-hand side
+    float2 *summ;  // segment summaries of this problem / right-hand side
+};
+
+// Returns false when the item's problem is inactive or has no iteration j.
+__device__ __forceinline__ bool load_item(const RefProb *__restrict__ probs, const int4 *__restrict__ items,
+                                          const int *__restrict__ active, int j, float *ck, float2 *summ,
+                                          ItemView &v)
+{
+    const int4 it = items[blockIdx.x];
+    const RefProb &p = probs[it.x];
+    if (!active[it.x] || j >= p.J) return false;
+    v.n = p.n;
+    v.ld = p.ld;
+    v.Ls = p.Ls;
+    v.P = p.P;
+    v.nchunk = p.nchunk;
+    v.seg = it.w;
+    v.k0 = it.z * kRC;
+    v.fac = p.fac + (int64_t)j * p.n;
+    v.phick = p.phick + (int64_t)j * 2 * p.nchunk;
+    v.segc = p.segc + (int64_t)j * 2 * p.P;
+    v.q2 = p.q2[j];
+    v.off = p.off32 + (int64_t)it.y * p.rhs32;
+    v.ck = ck + p.offck + (int64_t)it.y * p.rhsck;
+    v.summ = summ + p.offsm + (int64_t)it.y * p.rhssm;
+    return true;
+}
 
 // ---------------------------------------------------------------------------
-// Partitioned elimination.  Each (column, parity) system of m rows is cut into
-// P segments of Ls rows (Ls a multiple of kChunk); one warp owns one segment of
-// 32 columns.  With the true forward value z_in entering a segment and the true
-// back-substitution value x_out leaving it,
-//     z_t = zl_t + Phi_t z_in                 (zl: forward sweep started from 0)
-//     x_start = a + B z_in + Psi x_out,        a = sum_t kappa_t zl_t
-// where Phi_t = prod(-lf), kappa_t = ip_t prod_{u<t}(-uf_u), Psi = prod(-uf),
-// B = sum kappa_t Phi_t depend only on the shift (precomputed per shift).
-// Kernel 1 runs the local forward sweeps, checkpoints zl every kChunk rows and
-// writes (zl_end, a) per segment; kernel 2 chains the segments (O(P) per warp),
-// then recomputes each chunk from its checkpoint (converted to the true z) in
-// reverse order and back-substitutes.  Every input is read twice, every output
-// written once, and the segments multiply the number of independent warps.
+// Pass kernel 1: local forward sweeps of one segment (NR right-hand sides).
 // ---------------------------------------------------------------------------
 template <int NR, int DS>
 struct FwdSmem {
@@ -72,25 +108,30 @@ struct FwdSmem {
 };
 
 template <int NR, int DS>
-__global__ void __launch_bounds__(64) fwd_local_kernel(const float *__restrict__ In0, const float *__restrict__ In1,
-                                                       float *__restrict__ ck, float2 *__restrict__ summ,
-                                                       const float4 *__restrict__ fac, int n, int ld, int Ls)
+__global__ void __launch_bounds__(64) fwd_local_kernel(const RefProb *__restrict__ probs,
+                                                       const int4 *__restrict__ items, const int *__restrict__ active,
+                                                       int j, const float *__restrict__ In0,
+                                                       const float *__restrict__ In1, float *__restrict__ ckbase,
+                                                       float2 *__restrict__ summbase)
 {
     __shared__ __align__(16) FwdSmem<NR, DS> S;
+    ItemView v;
+    if (!load_item(probs, items, active, j, ckbase, summbase, v)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, par = w;
-    const int k0 = blockIdx.x * kRC, seg = blockIdx.y;
+    const int n = v.n, ld = v.ld, k0 = v.k0;
     const int m = (n - par + 1) / 2;
-    const int tb = seg * Ls;
-    const int te = min(tb + Ls, m);
+    const int tb = v.seg * v.Ls;
+    const int te = min(tb + v.Ls, m);
     const int nrows = max(te - tb, 0);
     const int nslot = (nrows + kU - 1) / kU;
     const int rsub = lane >> 3, piece = lane & 7;
-    const float *in[2] = {In0, In1};
+    const float *in[2] = {In0 + v.off, (NR > 1 ? In1 : In0) + v.off};
+    const float4 *fac = v.fac;
 
-    auto issue = [&](int v) {
-        if (v < nslot) {
-            const int b = v % DS;
-            const int t = tb + v * kU + rsub;
+    auto issue = [&](int s) {
+        if (s < nslot) {
+            const int b = s % DS;
+            const int t = tb + s * kU + rsub;
             if (t < te) {
                 const int i = par + 2 * t;
 #pragma unroll
@@ -101,19 +142,19 @@ __global__ void __launch_bounds__(64) fwd_local_kernel(const float *__restrict__
         cp_commit();
     };
 #pragma unroll
-    for (int v = 0; v < DS - 1; ++v) issue(v);
+    for (int s = 0; s < DS - 1; ++s) issue(s);
     float z[NR], a[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) z[r] = a[r] = 0.f;
-    for (int v = 0; v < nslot; ++v) {
+    for (int s = 0; s < nslot; ++s) {
         __syncwarp();
-        issue(v + DS - 1);
+        issue(s + DS - 1);
         cp_wait<DS - 1>();
         __syncwarp();
-        const int b = v % DS;
+        const int b = s % DS;
 #pragma unroll
         for (int rr = 0; rr < kU; ++rr) {
-            const int t = tb + v * kU + rr;
+            const int t = tb + s * kU + rr;
             if (t < te) {
                 const float4 f = S.fring[w][b][rr];
 #pragma unroll
@@ -124,96 +165,127 @@ __global__ void __launch_bounds__(64) fwd_local_kernel(const float *__restrict__
                 if ((t & (kChunk - 1)) == kChunk - 1) {
                     const int c = t / kChunk;
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) ck[((c * 2 + par) * NR + r) * ld + k0 + lane] = z[r];
+                    for (int r = 0; r < NR; ++r) v.ck[((c * 2 + par) * NR + r) * ld + k0 + lane] = z[r];
                 }
             }
         }
     }
     cp_wait<0>();
 #pragma unroll
-    for (int r = 0; r < NR; ++r) summ[((seg * 2 + par) * NR + r) * ld + k0 + lane] = make_float2(z[r], a[r]);
+    for (int r = 0; r < NR; ++r) v.summ[((v.seg * 2 + par) * NR + r) * ld + k0 + lane] = make_float2(z[r], a[r]);
 }
 
-// Chain the segments of this warp's (column, parity) systems: true z entering
-// segment `seg` and true x leaving it, for each of the NR right-hand sides.
+// Chain the segments of this lane's (column, parity) system for right-hand side r:
+// the true z entering segment `seg` and the true x leaving it, in one ascending
+// pass:  z_in(s+1) = zl_end(s) + Phi_end(s) z_in(s);
+//        x_out(seg) = sum_{s > seg} (a_s + B_s z_in(s)) prod_{seg < s' < s} Psi_s'.
 template <int NR>
-__device__ __forceinline__ void segment_chain(const float2 *__restrict__ summ, const float4 *__restrict__ segc,
-                                              int P, int seg, int par, int ld, int kcol, float (*zin_s)[32],
-                                              int lane, float *zin, float *xout)
+__device__ __forceinline__ void segment_chain(const ItemView &v, int par, int r, int kcol, float &zin, float &xout)
 {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        float zi = 0.f;
-        for (int s = 0; s < P; ++s) {
-            zin_s[s][lane] = zi;
-            const float2 ea = summ[((s * 2 + par) * NR + r) * ld + kcol];
-            zi = fmaf(segc[par * P + s].x, zi, ea.x);
+    float zi = 0.f, xo = 0.f, prod = 1.f;
+    zin = 0.f;
+    for (int s = 0; s < v.P; ++s) {
+        const float2 ea = v.summ[((s * 2 + par) * NR + r) * v.ld + kcol];
+        const float4 sc = v.segc[par * v.P + s];
+        if (s == v.seg) zin = zi;
+        if (s > v.seg) {
+            xo = fmaf(fmaf(sc.z, zi, ea.y), prod, xo);
+            prod *= sc.y;
         }
-        float xs = 0.f;
-        for (int s = P - 1; s > seg; --s) {
-            const float2 ea = summ[((s * 2 + par) * NR + r) * ld + kcol];
-            const float4 sc = segc[par * P + s];
-            xs = fmaf(sc.y, xs, fmaf(sc.z, zin_s[s][lane], ea.y));
+        zi = fmaf(sc.x, zi, ea.x);
+    }
+    xout = xo;
+}
+
+// Chunk slots of pass kernel 2: chunks from last to first, rows ascending inside.
+struct SlotMap {
+    int cend, cfirst, last_slots, nslot, te;
+    __device__ __forceinline__ void at(int s, int &c, int &t) const
+    {
+        if (s < last_slots) {
+            c = cend - 1;
+            t = c * kChunk + s * kU;
+        } else {
+            const int u = s - last_slots;
+            c = cend - 2 - u / (kChunk / kU);
+            t = c * kChunk + (u % (kChunk / kU)) * kU;
         }
-        zin[r] = zin_s[seg][lane];
-        xout[r] = xs;
-        __syncwarp();
+    }
+};
+__device__ __forceinline__ SlotMap make_slots(int tb, int te, int Ls, int m0)
+{
+    SlotMap sm;
+    sm.cfirst = tb / kChunk;
+    sm.cend = (min(tb + Ls, m0) + kChunk - 1) / kChunk;
+    const int last_len = max(min(te, sm.cend * kChunk) - (sm.cend - 1) * kChunk, 0);
+    sm.last_slots = (last_len + kU - 1) / kU;
+    sm.nslot = (te > tb) ? sm.last_slots + (sm.cend - 1 - sm.cfirst) * (kChunk / kU) : 0;
+    sm.te = te;
+    return sm;
+}
+
+// Transposed store of a 32 x 64 tile: Out[(k0 + cc) * ld + ibase + rr] for
+// cc < 32 (k0 + cc < n), rr < 64 (ibase + rr < ld), four rows per 16-byte store.
+// Rows beyond n inside the padded leading dimension receive don't-care values.
+__device__ __forceinline__ void store_tile(float *__restrict__ out, const float (*tile)[kTileRows + 1], int k0,
+                                           int ibase, int n, int ld)
+{
+    const int lim = min(kTileRows, ld - ibase);
+    for (int idx = threadIdx.x; idx < kRC * (kTileRows / 4); idx += 64) {
+        const int cc = idx / (kTileRows / 4), r4 = (idx % (kTileRows / 4)) * 4;
+        if (k0 + cc < n && r4 < lim) {
+            const float4 val = make_float4(tile[cc][r4], tile[cc][r4 + 1], tile[cc][r4 + 2], tile[cc][r4 + 3]);
+            *reinterpret_cast<float4 *>(out + (int64_t)(k0 + cc) * ld + ibase + r4) = val;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Row pass, kernel 2.  Input Pt = rho^T (solve down its columns).
-// Outputs (stored transposed, i.e. in rho's orientation): A = a, C = c = rho + 2q a.
+// Row pass, kernel 2.  Input rho^T (solve down its columns).  Outputs stored
+// transposed (in rho's orientation): a and c = rho + 2q a.
 // ---------------------------------------------------------------------------
 template <int DS>
 struct RowBwdSmem {
     float ring[2][DS][kU][32];
     float4 fring[2][DS][kU];
-    float zb[2][kChunk][32];    // ip * z of the chunk
-    float rb[2][kChunk][32];    // rho of the chunk
+    float zb[2][kChunk][32];  // ip * z of the chunk
+    float rb[2][kChunk][32];  // rho of the chunk
     float ufb[2][kChunk];
-    float zin_s[2][kMaxSeg][32];
     float tileA[kRC][kTileRows + 1];
     float tileC[kRC][kTileRows + 1];
 };
 
 template <int DS>
-__global__ void __launch_bounds__(64) row_bwd_kernel(const float *__restrict__ Pt, float *__restrict__ Aout,
-                                                     float *__restrict__ Cout, const float *__restrict__ ck,
-                                                     const float2 *__restrict__ summ, const float4 *__restrict__ fac,
-                                                     const float *__restrict__ phick, const float4 *__restrict__ segc,
-                                                     float q2, int n, int ld, int Ls, int P, int nchunk)
+__global__ void __launch_bounds__(64) row_bwd_kernel(const RefProb *__restrict__ probs,
+                                                     const int4 *__restrict__ items, const int *__restrict__ active,
+                                                     int j, const float *__restrict__ Ptb, float *__restrict__ Ab,
+                                                     float *__restrict__ Cb, float *__restrict__ ckbase,
+                                                     float2 *__restrict__ summbase)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RowBwdSmem<DS> &S = *reinterpret_cast<RowBwdSmem<DS> *>(smem_raw);
+    ItemView v;
+    if (!load_item(probs, items, active, j, ckbase, summbase, v)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, par = w;
-    const int k0 = blockIdx.x * kRC, seg = blockIdx.y;
+    const int n = v.n, ld = v.ld, k0 = v.k0;
     const int m = (n - par + 1) / 2, m0 = (n + 1) / 2;
-    const int tb = seg * Ls;
-    const int te = min(tb + Ls, m);
-    const int cfirst = tb / kChunk;
-    const int cend = (min(tb + Ls, m0) + kChunk - 1) / kChunk;  // same for both warps
+    const int tb = v.seg * v.Ls;
+    const int te = min(tb + v.Ls, m);
     const int rsub = lane >> 3, piece = lane & 7;
+    const float *Pt = Ptb + v.off;
+    float *Aout = Ab + v.off, *Cout = Cb + v.off;
+    const float4 *fac = v.fac;
+    const float q2 = v.q2;
 
     float zin, xout;
-    segment_chain<1>(summ, segc, P, seg, par, ld, k0 + lane, S.zin_s[w], lane, &zin, &xout);
+    segment_chain<1>(v, par, 0, k0 + lane, zin, xout);
 
-    // slots: chunks from last to first, rows ascending in each chunk
-    const int last_len = max(min(te, cend * kChunk) - (cend - 1) * kChunk, 0);
-    const int last_slots = (last_len + kU - 1) / kU;
-    const int nslot = (te > tb) ? last_slots + (cend - 1 - cfirst) * (kChunk / kU) : 0;
-    auto issue = [&](int v) {
-        if (v < nslot) {
-            const int b = v % DS;
+    const SlotMap sm = make_slots(tb, te, v.Ls, m0);
+    auto issue = [&](int s) {
+        if (s < sm.nslot) {
+            const int b = s % DS;
             int c, t;
-            if (v < last_slots) {
-                c = cend - 1;
-                t = c * kChunk + v * kU;
-            } else {
-                const int u = v - last_slots;
-                c = cend - 2 - u / (kChunk / kU);
-                t = c * kChunk + (u % (kChunk / kU)) * kU;
-            }
+            sm.at(s, c, t);
             const int tr = t + rsub;
             if (tr < min((c + 1) * kChunk, te)) {
                 const int i = par + 2 * tr;
@@ -224,21 +296,21 @@ __global__ void __launch_bounds__(64) row_bwd_kernel(const float *__restrict__ P
         cp_commit();
     };
 #pragma unroll
-    for (int v = 0; v < DS - 1; ++v) issue(v);
-    int v = 0;
+    for (int s = 0; s < DS - 1; ++s) issue(s);
+    int s = 0;
     float x = xout;
-    const float *phi = phick + par * nchunk;
-    for (int c = cend - 1; c >= cfirst; --c) {
+    const float *phi = v.phick + par * v.nchunk;
+    for (int c = sm.cend - 1; c >= sm.cfirst; --c) {
         const int t0 = c * kChunk;
         const int t1 = min(t0 + kChunk, te);
         float zz = zin;
-        if (c > cfirst && t0 < te) zz = fmaf(phi[c - 1], zin, ck[((c - 1) * 2 + par) * ld + k0 + lane]);
-        for (int ts = t0; ts < t1; ts += kU, ++v) {
+        if (c > sm.cfirst && t0 < te) zz = fmaf(phi[c - 1], zin, v.ck[((c - 1) * 2 + par) * ld + k0 + lane]);
+        for (int ts = t0; ts < t1; ts += kU, ++s) {
             __syncwarp();
-            issue(v + DS - 1);
+            issue(s + DS - 1);
             cp_wait<DS - 1>();
             __syncwarp();
-            const int b = v % DS;
+            const int b = s % DS;
 #pragma unroll
             for (int rr = 0; rr < kU; ++rr) {
                 const int t = ts + rr;
@@ -253,116 +325,108 @@ __global__ void __launch_bounds__(64) row_bwd_kernel(const float *__restrict__ P
             }
         }
         __syncwarp();
-        for (int t = t1 - 1; t >= t0; --t) {
-            const int tt = t - t0;
-            x = fmaf(-S.ufb[w][tt], x, S.zb[w][tt][lane]);
-            S.tileA[lane][2 * tt + par] = x;
-            S.tileC[lane][2 * tt + par] = fmaf(q2, x, S.rb[w][tt][lane]);
-        }
-        __syncthreads();
-        const int ibase = c * kTileRows;
-        const int rows = min(kTileRows, n - ibase);
-        for (int idx = threadIdx.x; idx < kRC * kTileRows; idx += 64) {
-            const int cc = idx / kTileRows, rr = idx % kTileRows;
-            if (k0 + cc < n && rr < rows) {
-                const int o = (k0 + cc) * ld + ibase + rr;
-                Aout[o] = S.tileA[cc][rr];
-                Cout[o] = S.tileC[cc][rr];
+#pragma unroll 8
+        for (int tt = kChunk - 1; tt >= 0; --tt) {
+            if (t0 + tt < t1) {
+                x = fmaf(-S.ufb[w][tt], x, S.zb[w][tt][lane]);
+                S.tileA[lane][2 * tt + par] = x;
+                S.tileC[lane][2 * tt + par] = fmaf(q2, x, S.rb[w][tt][lane]);
             }
         }
+        __syncthreads();
+        store_tile(Aout, S.tileA, k0, c * kTileRows, n, ld);
+        store_tile(Cout, S.tileC, k0, c * kTileRows, n, ld);
         __syncthreads();
     }
     cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
-// Column pass, kernel 2.  Inputs C = c, A = a (solve down columns), Dl = D.
-// Outputs: Pt = (c + 2q g)^T (transposed store), Dl -= 2q b (Dl = -2q b when first).
+// Column pass, kernel 2.  Inputs c, a (solve down columns), D.  Outputs rho+ =
+// c + 2q g stored transposed, D -= 2q b in place (D = -2q b when FIRST).  The D
+// values of a chunk are loaded into registers while the chunk is recomputed.
 // ---------------------------------------------------------------------------
 template <int DS>
 struct ColBwdSmem {
-    float ring[2][DS][3][kU][32];
+    float ring[2][DS][2][kU][32];
     float4 fring[2][DS][kU];
     float zc[2][kChunk][32];
     float za[2][kChunk][32];
     float cb[2][kChunk][32];
-    float db[2][kChunk][32];
     float ufb[2][kChunk];
-    float zin_s[2][kMaxSeg][32];
     float tile[kRC][kTileRows + 1];
 };
 
 template <int DS, bool FIRST>
-__global__ void __launch_bounds__(64) col_bwd_kernel(const float *__restrict__ Cin, const float *__restrict__ Ain,
-                                                     float *__restrict__ Dl, float *__restrict__ Pt,
-                                                     const float *__restrict__ ck, const float2 *__restrict__ summ,
-                                                     const float4 *__restrict__ fac, const float *__restrict__ phick,
-                                                     const float4 *__restrict__ segc, float q2, int n, int ld, int Ls,
-                                                     int P, int nchunk)
+__global__ void __launch_bounds__(64) col_bwd_kernel(const RefProb *__restrict__ probs,
+                                                     const int4 *__restrict__ items, const int *__restrict__ active,
+                                                     int j, const float *__restrict__ Cb, const float *__restrict__ Ab,
+                                                     float *__restrict__ Db, float *__restrict__ Ptb,
+                                                     float *__restrict__ ckbase, float2 *__restrict__ summbase)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ColBwdSmem<DS> &S = *reinterpret_cast<ColBwdSmem<DS> *>(smem_raw);
+    ItemView v;
+    if (!load_item(probs, items, active, j, ckbase, summbase, v)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, par = w;
-    const int k0 = blockIdx.x * kRC, seg = blockIdx.y;
+    const int n = v.n, ld = v.ld, k0 = v.k0;
     const int k = k0 + lane;
     const bool kin = k < n;
     const int m = (n - par + 1) / 2, m0 = (n + 1) / 2;
-    const int tb = seg * Ls;
-    const int te = min(tb + Ls, m);
-    const int cfirst = tb / kChunk;
-    const int cend = (min(tb + Ls, m0) + kChunk - 1) / kChunk;
+    const int tb = v.seg * v.Ls;
+    const int te = min(tb + v.Ls, m);
     const int rsub = lane >> 3, piece = lane & 7;
+    const float *Cin = Cb + v.off, *Ain = Ab + v.off;
+    float *Dl = Db + v.off, *Pt = Ptb + v.off;
+    const float4 *fac = v.fac;
+    const float q2 = v.q2;
 
-    float zin[2], xout[2];
-    segment_chain<2>(summ, segc, P, seg, par, ld, k, S.zin_s[w], lane, zin, xout);
+    float zin0, zin1, g, bb;
+    segment_chain<2>(v, par, 0, k, zin0, g);
+    segment_chain<2>(v, par, 1, k, zin1, bb);
 
-    const int last_len = max(min(te, cend * kChunk) - (cend - 1) * kChunk, 0);
-    const int last_slots = (last_len + kU - 1) / kU;
-    const int nslot = (te > tb) ? last_slots + (cend - 1 - cfirst) * (kChunk / kU) : 0;
-    auto issue = [&](int v) {
-        if (v < nslot) {
-            const int b = v % DS;
+    const SlotMap sm = make_slots(tb, te, v.Ls, m0);
+    auto issue = [&](int s) {
+        if (s < sm.nslot) {
+            const int b = s % DS;
             int c, t;
-            if (v < last_slots) {
-                c = cend - 1;
-                t = c * kChunk + v * kU;
-            } else {
-                const int u = v - last_slots;
-                c = cend - 2 - u / (kChunk / kU);
-                t = c * kChunk + (u % (kChunk / kU)) * kU;
-            }
+            sm.at(s, c, t);
             const int tr = t + rsub;
             if (tr < min((c + 1) * kChunk, te)) {
                 const int i = par + 2 * tr;
                 const int o = i * ld + k0 + piece * 4;
                 cp16(&S.ring[w][b][0][rsub][piece * 4], Cin + o);
                 cp16(&S.ring[w][b][1][rsub][piece * 4], Ain + o);
-                if (!FIRST) cp16(&S.ring[w][b][2][rsub][piece * 4], Dl + o);
                 if (piece == 0) cp16(&S.fring[w][b][rsub], fac + i);
             }
         }
         cp_commit();
     };
 #pragma unroll
-    for (int v = 0; v < DS - 1; ++v) issue(v);
-    int v = 0;
-    float g = xout[0], bb = xout[1];
-    const float *phi = phick + par * nchunk;
-    for (int c = cend - 1; c >= cfirst; --c) {
+    for (int s = 0; s < DS - 1; ++s) issue(s);
+    int s = 0;
+    const float *phi = v.phick + par * v.nchunk;
+    for (int c = sm.cend - 1; c >= sm.cfirst; --c) {
         const int t0 = c * kChunk;
         const int t1 = min(t0 + kChunk, te);
-        float zzc = zin[0], zza = zin[1];
-        if (c > cfirst && t0 < te) {
-            const float ph = phi[c - 1];
-            zzc = fmaf(ph, zin[0], ck[(((c - 1) * 2 + par) * 2 + 0) * ld + k]);
-            zza = fmaf(ph, zin[1], ck[(((c - 1) * 2 + par) * 2 + 1) * ld + k]);
+        float dreg[kChunk];
+        if (!FIRST) {
+#pragma unroll
+            for (int tt = 0; tt < kChunk; ++tt)
+                dreg[tt] = (kin && t0 + tt < t1) ? Dl[(par + 2 * (t0 + tt)) * ld + k] : 0.f;
         }
-        for (int ts = t0; ts < t1; ts += kU, ++v) {
+        float zzc = zin0, zza = zin1;
+        if (c > sm.cfirst && t0 < te) {
+            const float ph = phi[c - 1];
+            zzc = fmaf(ph, zin0, v.ck[(((c - 1) * 2 + par) * 2 + 0) * ld + k]);
+            zza = fmaf(ph, zin1, v.ck[(((c - 1) * 2 + par) * 2 + 1) * ld + k]);
+        }
+        for (int ts = t0; ts < t1; ts += kU, ++s) {
             __syncwarp();
-            issue(v + DS - 1);
+            issue(s + DS - 1);
             cp_wait<DS - 1>();
             __syncwarp();
-            const int b = v % DS;
+            const int b = s % DS;
 #pragma unroll
             for (int rr = 0; rr < kU; ++rr) {
                 const int t = ts + rr;
@@ -375,163 +439,216 @@ __global__ void __launch_bounds__(64) col_bwd_kernel(const float *__restrict__ C
                     S.zc[w][tt][lane] = zzc * f.x;
                     S.za[w][tt][lane] = zza * f.x;
                     S.cb[w][tt][lane] = cv;
-                    if (!FIRST) S.db[w][tt][lane] = S.ring[w][b][2][rr][lane];
                     if (lane == 0) S.ufb[w][tt] = f.y;
                 }
             }
         }
         __syncwarp();
-        for (int t = t1 - 1; t >= t0; --t) {
-            const int tt = t - t0;
-            const float uf = S.ufb[w][tt];
-            g = fmaf(-uf, g, S.zc[w][tt][lane]);
-            bb = fmaf(-uf, bb, S.za[w][tt][lane]);
-            S.tile[lane][2 * tt + par] = fmaf(q2, g, S.cb[w][tt][lane]);
-            if (kin) Dl[(par + 2 * t) * ld + k] = FIRST ? -q2 * bb : fmaf(-q2, bb, S.db[w][tt][lane]);
+#pragma unroll
+        for (int tt = kChunk - 1; tt >= 0; --tt) {
+            if (t0 + tt < t1) {
+                const float uf = S.ufb[w][tt];
+                g = fmaf(-uf, g, S.zc[w][tt][lane]);
+                bb = fmaf(-uf, bb, S.za[w][tt][lane]);
+                S.tile[lane][2 * tt + par] = fmaf(q2, g, S.cb[w][tt][lane]);
+                if (kin) Dl[(par + 2 * (t0 + tt)) * ld + k] = FIRST ? -q2 * bb : fmaf(-q2, bb, dreg[tt]);
+            }
         }
         __syncthreads();
-        const int ibase = c * kTileRows;
-        const int rows = min(kTileRows, n - ibase);
-        for (int idx = threadIdx.x; idx < kRC * kTileRows; idx += 64) {
-            const int cc = idx / kTileRows, rr = idx % kTileRows;
-            if (k0 + cc < n && rr < rows) Pt[(k0 + cc) * ld + ibase + rr] = S.tile[cc][rr];
-        }
+        store_tile(Pt, S.tile, k0, c * kTileRows, n, ld);
         __syncthreads();
     }
     cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
-// FP64 residual with the pending correction folded in:
-//   Yout = Y + s * D ;  R = F~ - A~ Yout - Yout A~ ;  Pt = (R / s)^T in FP32 ;  rmax = max |R|
-// 32x32 output tile per CTA with a halo of two in both directions.  Y and Yout
-// are distinct buffers, so every CTA sees the same not-yet-updated halo.
+// FP64 kernels over 32 x 32 tiles of every (problem, right-hand side).
+// A tile item is {problem * 256 + rhs, tile column, tile row, 0}.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) residual_kernel(const double *__restrict__ Y, double *__restrict__ Yout,
-                                                       const float *__restrict__ Dl,
-                                                       const double *__restrict__ Ft, float *__restrict__ Pt,
-                                                       const double *__restrict__ dband,
-                                                       const double *__restrict__ eband,
-                                                       const unsigned long long *__restrict__ s_bits, int64_t n,
-                                                       int64_t ld, unsigned long long *__restrict__ rmax,
-                                                       int apply_update, int y_zero)
+struct TileView {
+    int n, ld;
+    int64_t off64, off32;
+    const double *d, *e, *s;
+    int idx;  // index of the (problem, rhs) pair for per-pair scalars
+    int64_t bx, by;
+};
+__device__ __forceinline__ TileView load_tile(const RefProb64 *__restrict__ probs, const int4 *__restrict__ tiles)
 {
-    const double s = __longlong_as_double((long long)*s_bits);
-    const double inv_s = 1.0 / s;
+    const int4 t = tiles[blockIdx.x];
+    const RefProb64 &p = probs[t.x >> 8];
+    const int rhs = t.x & 255;
+    TileView v;
+    v.n = p.n;
+    v.ld = p.ld;
+    v.off64 = p.off64 + (int64_t)rhs * p.n * p.n;
+    v.off32 = p.off32 + (int64_t)rhs * p.rhs32;
+    v.d = p.d;
+    v.e = p.e;
+    v.s = p.s;
+    v.idx = p.pair0 + rhs;
+    v.bx = (int64_t)t.y * 32;
+    v.by = (int64_t)t.z * 32;
+    return v;
+}
+
+__device__ __forceinline__ double flag_nonfinite(double a, double local)
+{
+    // NaN and Inf both become +Inf so that the maximum flags them (fmax drops NaN)
+    return (a <= 1.7976931348623157e308) ? fmax(local, a) : __longlong_as_double(0x7ff0000000000000LL);
+}
+
+__device__ __forceinline__ void block_max_to(double local, unsigned long long *out)
+{
+    for (int off = 16; off > 0; off >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, off));
+    __shared__ double wmax[8];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (tx == 0) wmax[ty] = local;
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+        double bm = 0.0;
+        for (int t = 0; t < (int)blockDim.y; ++t) bm = fmax(bm, wmax[t]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(bm));
+    }
+}
+
+// max |D_s F D_s| per (problem, rhs)
+__global__ void __launch_bounds__(256) absmax_tiles_kernel(const RefProb64 *__restrict__ probs,
+                                                           const int4 *__restrict__ tiles,
+                                                           const double *__restrict__ F,
+                                                           unsigned long long *__restrict__ smax)
+{
+    const TileView v = load_tile(probs, tiles);
+    double local = 0.0;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t i = v.by + r, kk = v.bx + threadIdx.x;
+        if (i < v.n && kk < v.n) local = flag_nonfinite(fabs(F[v.off64 + i * v.n + kk] * v.s[i] * v.s[kk]), local);
+    }
+    block_max_to(local, smax + v.idx);
+}
+
+// F~ = D_s F D_s (FP64) and rho0^T = (F~ / s)^T (FP32, ld-strided)
+__global__ void __launch_bounds__(256) scale_in_tiles_kernel(const RefProb64 *__restrict__ probs,
+                                                             const int4 *__restrict__ tiles,
+                                                             const double *__restrict__ F, double *__restrict__ Ft,
+                                                             float *__restrict__ Pt,
+                                                             const unsigned long long *__restrict__ smax)
+{
+    __shared__ float t[32][33];
+    const TileView v = load_tile(probs, tiles);
+    const double sF = __longlong_as_double((long long)smax[v.idx]);
+    const double inv_s = sF > 0.0 ? 1.0 / sF : 0.0;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t i = v.by + r, kk = v.bx + threadIdx.x;
+        float v32 = 0.f;
+        if (i < v.n && kk < v.n) {
+            const double val = F[v.off64 + i * v.n + kk] * v.s[i] * v.s[kk];
+            Ft[v.off64 + i * v.n + kk] = val;
+            v32 = (float)(val * inv_s);
+        }
+        t[r][threadIdx.x] = v32;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t kk = v.bx + r, i = v.by + threadIdx.x;
+        if (i < v.n && kk < v.n) Pt[v.off32 + kk * v.ld + i] = t[threadIdx.x][r];
+    }
+}
+
+// Yout = Y + s D ; R = F~ - A~ Yout - Yout A~ ; Pt = (R / s)^T ; rmax = max |R|.
+// Y and Yout are distinct buffers, so every CTA sees the same not-yet-updated halo.
+// Right-hand sides that have converged only copy Y to Yout.
+__global__ void __launch_bounds__(256) residual_tiles_kernel(const RefProb64 *__restrict__ probs,
+                                                             const int4 *__restrict__ tiles,
+                                                             const double *__restrict__ Y, double *__restrict__ Yout,
+                                                             const float *__restrict__ Dl,
+                                                             const double *__restrict__ Ft, float *__restrict__ Pt,
+                                                             const unsigned long long *__restrict__ smax,
+                                                             unsigned long long *__restrict__ rmax,
+                                                             const int *__restrict__ pair_active, int y_zero)
+{
     __shared__ double Ys[36][37];
     __shared__ float Ts[32][33];
-    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    // load the 36 x 36 window (rows by-2..by+33, cols bx-2..bx+33) of the updated iterate
+    const TileView v = load_tile(probs, tiles);
+    if (!pair_active[v.idx]) {
+        // converged right-hand side: carry its iterate over to the other buffer unchanged
+        for (int r = threadIdx.y; r < 32; r += 8) {
+            const int64_t i = v.by + r, kk = v.bx + threadIdx.x;
+            if (i < v.n && kk < v.n) Yout[v.off64 + i * v.n + kk] = y_zero ? 0.0 : Y[v.off64 + i * v.n + kk];
+        }
+        return;
+    }
+    const double sF = __longlong_as_double((long long)smax[v.idx]);
+    const double inv_s = sF > 0.0 ? 1.0 / sF : 0.0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t n = v.n;
     for (int r = ty; r < 36; r += 8) {
-        const int64_t i = by - 2 + r;
+        const int64_t i = v.by - 2 + r;
         for (int cc = tx; cc < 36; cc += 32) {
-            const int64_t kk = bx - 2 + cc;
-            double v = 0.0;
+            const int64_t kk = v.bx - 2 + cc;
+            double val = 0.0;
             if (i >= 0 && i < n && kk >= 0 && kk < n) {
-                v = y_zero ? 0.0 : Y[i * n + kk];
-                if (apply_update) v = fma(s, (double)Dl[i * ld + kk], v);
+                val = y_zero ? 0.0 : Y[v.off64 + i * n + kk];
+                val = fma(sF, (double)Dl[v.off32 + i * v.ld + kk], val);
             }
-            Ys[r][cc] = v;
+            Ys[r][cc] = val;
         }
     }
     __syncthreads();
     double local = 0.0;
     for (int r = ty; r < 32; r += 8) {
-        const int64_t i = by + r;
-        const int64_t kk = bx + tx;
+        const int64_t i = v.by + r;
+        const int64_t kk = v.bx + tx;
         float out = 0.f;
         if (i < n && kk < n) {
             const double y = Ys[r + 2][tx + 2];
-            double acc = Ft[i * n + kk];
-            acc = fma(-(dband[i] + dband[kk]), y, acc);
-            if (i >= 2) acc = fma(-eband[i - 2], Ys[r][tx + 2], acc);
-            acc = fma(-eband[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
-            if (kk >= 2) acc = fma(-eband[kk - 2], Ys[r + 2][tx], acc);
-            acc = fma(-eband[kk], Ys[r + 2][tx + 4], acc);
-            if (apply_update) Yout[i * n + kk] = y;
-            const double aa = fabs(acc);
-            local = (aa <= 1.7976931348623157e308) ? fmax(local, aa) : __longlong_as_double(0x7ff0000000000000LL);
+            double acc = Ft[v.off64 + i * n + kk];
+            acc = fma(-(v.d[i] + v.d[kk]), y, acc);
+            if (i >= 2) acc = fma(-v.e[i - 2], Ys[r][tx + 2], acc);
+            acc = fma(-v.e[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
+            if (kk >= 2) acc = fma(-v.e[kk - 2], Ys[r + 2][tx], acc);
+            acc = fma(-v.e[kk], Ys[r + 2][tx + 4], acc);
+            Yout[v.off64 + i * n + kk] = y;
+            local = flag_nonfinite(fabs(acc), local);
             out = (float)(acc * inv_s);
         }
         Ts[r][tx] = out;
     }
     __syncthreads();
-    // transposed FP32 store: Pt[k][i]
     for (int r = ty; r < 32; r += 8) {
-        const int64_t kk = bx + r, i = by + tx;
-        if (kk < n && i < n) Pt[kk * ld + i] = Ts[tx][r];
+        const int64_t kk = v.bx + r, i = v.by + tx;
+        if (kk < n && i < n) Pt[v.off32 + kk * v.ld + i] = Ts[tx][r];
     }
-    // block max -> global max (non-negative doubles order like their bit patterns)
-    for (int off = 16; off > 0; off >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, off));
-    __shared__ double wmax[8];
-    if (tx == 0) wmax[ty] = local;
-    __syncthreads();
-    if (tx == 0 && ty == 0) {
-        double bm = 0.0;
-        for (int t = 0; t < 8; ++t) bm = fmax(bm, wmax[t]);
-        atomicMax(rmax, (unsigned long long)__double_as_longlong(bm));
-    }
+    block_max_to(local, rmax + v.idx);
 }
 
-// Scale-in for the refinement: F~ = D_s F D_s (FP64, n x n), rho0^T = (F~ / s)^T
-// in FP32 (ld-strided), and max |F~|.
-__global__ void __launch_bounds__(256) refine_scale_in_kernel(const double *__restrict__ F, double *__restrict__ Ft,
-                                                              float *__restrict__ Pt, const double *__restrict__ sc,
-                                                              int64_t n, int64_t ld,
-                                                              const unsigned long long *__restrict__ s_bits)
+// X = D_s Y D_s
+__global__ void __launch_bounds__(256) scale_out_tiles_kernel(const RefProb64 *__restrict__ probs,
+                                                              const int4 *__restrict__ tiles,
+                                                              const double *__restrict__ Y, double *__restrict__ X)
 {
-    const double inv_s = 1.0 / __longlong_as_double((long long)*s_bits);
-    __shared__ float t[32][33];
-    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t i = by + r, kk = bx + threadIdx.x;
-        float v32 = 0.f;
-        if (i < n && kk < n) {
-            const double v = F[i * n + kk] * sc[i] * sc[kk];
-            Ft[i * n + kk] = v;
-            v32 = (float)(v * inv_s);
-        }
-        t[r][threadIdx.x] = v32;
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t kk = bx + r, i = by + threadIdx.x;
-        if (i < n && kk < n) Pt[kk * ld + i] = t[threadIdx.x][r];
+    const TileView v = load_tile(probs, tiles);
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t i = v.by + r, kk = v.bx + threadIdx.x;
+        if (i < v.n && kk < v.n) X[v.off64 + i * v.n + kk] = Y[v.off64 + i * v.n + kk] * v.s[i] * v.s[kk];
     }
 }
 
-__global__ void absmax_kernel(const double *__restrict__ F, const double *__restrict__ sc, int64_t n,
-                              unsigned long long *__restrict__ out)
-{
-    double local = 0.0;
-    const int64_t nn = n * n;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / n, kk = t - i * n;
-        const double a = fabs(F[t] * sc[i] * sc[kk]);
-        // NaN and Inf both become +Inf so that the maximum flags them (fmax drops NaN)
-        local = (a <= 1.7976931348623157e308) ? fmax(local, a) : __longlong_as_double(0x7ff0000000000000LL);
-    }
-    for (int off = 16; off > 0; off >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(local));
-}
-
-// FP32 factors of A~ - q I for the partitioned sweeps, from FP64 arithmetic:
+// FP32 factors of A~ - q I for the partitioned sweeps, from FP64 arithmetic, one
+// thread per (problem, shift, parity):
 //   fac[i]   = {1/den_i, e_i/den_i, e_{i-2}/den_{i-2}, kappa_i}
 //   phick[c] = Phi at the last row of chunk c (relative to its segment start)
 //   segc[s]  = {Phi_end, Psi, B, 0} of segment s ({1, 1, 0, 0} when empty)
-__global__ void factor32_kernel(const double *__restrict__ d, const double *__restrict__ e,
-                                const double *__restrict__ q, int J, int64_t n, int Ls, int P, int nchunk,
-                                float4 *__restrict__ fac, float *__restrict__ phick, float4 *__restrict__ segc)
+__global__ void factor32_kernel(const FactorJob *__restrict__ jobs, int njobs)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= 2 * J) return;
-    const int j = tid >> 1, par = tid & 1;
-    const double qj = q[j];
+    if (tid >= 2 * njobs) return;
+    const FactorJob &jb = jobs[tid >> 1];
+    const int par = tid & 1;
+    const double qj = jb.q;
+    const int64_t n = jb.n, Ls = jb.Ls;
     const int64_t m = (n - par + 1) / 2;
-    float4 *fj = fac + (int64_t)j * n;
-    float *pj = phick + ((int64_t)j * 2 + par) * nchunk;
-    float4 *sj = segc + ((int64_t)j * 2 + par) * P;
+    float *pj = jb.phick + par * jb.nchunk;
+    float4 *sj = jb.segc + par * jb.P;
     double uf_prev = 0.0, Phi = 1.0, prodU = 1.0, B = 0.0;
     for (int64_t t = 0; t < m; ++t) {
         const int64_t i = par + 2 * t;
@@ -540,23 +657,23 @@ __global__ void factor32_kernel(const double *__restrict__ d, const double *__re
             prodU = 1.0;
             B = 0.0;
         }
-        double den = d[i] - qj;
-        if (i >= 2) den -= e[i - 2] * uf_prev;
+        double den = jb.d[i] - qj;
+        if (i >= 2) den -= jb.e[i - 2] * uf_prev;
         const double ip = 1.0 / den;
-        const double uf = e[i] * ip;
+        const double uf = jb.e[i] * ip;
         const double lf = uf_prev;
         Phi *= -lf;
         const double kappa = ip * prodU;
         prodU *= -uf;
         B += kappa * Phi;
-        fj[i] = make_float4((float)ip, (float)uf, (float)lf, (float)kappa);
+        jb.fac[i] = make_float4((float)ip, (float)uf, (float)lf, (float)kappa);
         if (t % kChunk == kChunk - 1) pj[t / kChunk] = (float)Phi;
         const int64_t seg = t / Ls;
         const int64_t seg_end = ((seg + 1) * Ls < m) ? (seg + 1) * Ls : m;
         if (t == seg_end - 1) sj[seg] = make_float4((float)Phi, (float)prodU, (float)B, 0.f);
         uf_prev = uf;
     }
-    for (int64_t s = (m + Ls - 1) / Ls; s < P; ++s) sj[s] = make_float4(1.f, 1.f, 0.f, 0.f);
+    for (int64_t s = (m + Ls - 1) / Ls; s < jb.P; ++s) sj[s] = make_float4(1.f, 1.f, 0.f, 0.f);
 }
 
 constexpr int kDF = 12;  // ring depth (slots) of the forward kernels
@@ -569,7 +686,7 @@ size_t colb_smem() { return sizeof(ColBwdSmem<DS>); }
 
 }  // namespace
 
-RefineGeometry refine_geometry(int64_t n, int sms)
+RefineGeometry refine_geometry(int64_t n, int target_ctas)
 {
     RefineGeometry g;
     g.ld = (n + 31) / 32 * 32;
@@ -577,8 +694,8 @@ RefineGeometry refine_geometry(int64_t n, int sms)
     const int64_t nblk = (n + kRC - 1) / kRC;
     g.nblk = nblk;
     g.nchunk = (m0 + kChunk - 1) / kChunk;
-    // enough segments for ~16 warps per SM, at most kMaxSeg, each a whole number of chunks
-    int64_t want = (16LL * sms + 2 * nblk - 1) / (2 * nblk);
+    // enough segments for the requested number of CTAs, each a whole number of chunks
+    int64_t want = (target_ctas + nblk - 1) / nblk;
     if (want < 1) want = 1;
     if (want > kMaxSeg) want = kMaxSeg;
     int64_t Ls = (m0 + want - 1) / want;
@@ -605,76 +722,68 @@ cudaError_t refine_setup_kernels()
                                 (int)colb_smem<kDB>());
 }
 
-cudaError_t launch_row_pass(const float *Pt, float *A, float *C, const RefineScratch &w, const float4 *fac,
-                            const float *phick, const float4 *segc, float q2, int64_t n, const RefineGeometry &g,
-                            cudaStream_t st)
+cudaError_t launch_row_pass(const RefPassArgs &a, int j, cudaStream_t st)
 {
-    const dim3 grid((unsigned)g.nblk, (unsigned)g.P), block(64);
-    fwd_local_kernel<1, kDF><<<grid, block, 0, st>>>(Pt, nullptr, w.ck, w.summ, fac, (int)n, (int)g.ld, (int)g.Ls);
+    const dim3 grid((unsigned)a.nitems), block(64);
+    fwd_local_kernel<1, kDF><<<grid, block, 0, st>>>(a.probs, a.items, a.active, j, a.Pt, nullptr, a.ck, a.summ);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    row_bwd_kernel<kDB><<<grid, block, rowb_smem<kDB>(), st>>>(Pt, A, C, w.ck, w.summ, fac, phick, segc, q2, (int)n,
-                                                             (int)g.ld, (int)g.Ls, (int)g.P, (int)g.nchunk);
+    row_bwd_kernel<kDB><<<grid, block, rowb_smem<kDB>(), st>>>(a.probs, a.items, a.active, j, a.Pt, a.A, a.C, a.ck,
+                                                             a.summ);
     return cudaGetLastError();
 }
 
-cudaError_t launch_col_pass(const float *C, const float *A, float *Dl, float *Pt, const RefineScratch &w,
-                            const float4 *fac, const float *phick, const float4 *segc, float q2, int64_t n,
-                            const RefineGeometry &g, bool first, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
+cudaError_t launch_col_pass(const RefPassArgs &a, int j, bool first, cudaStream_t st, cudaEvent_t ev0,
+                            cudaEvent_t ev1)
 {
-    const dim3 grid((unsigned)g.nblk, (unsigned)g.P), block(64);
-    fwd_local_kernel<2, kDF><<<grid, block, 0, st>>>(C, A, w.ck, w.summ, fac, (int)n, (int)g.ld, (int)g.Ls);
+    const dim3 grid((unsigned)a.nitems), block(64);
+    fwd_local_kernel<2, kDF><<<grid, block, 0, st>>>(a.probs, a.items, a.active, j, a.C, a.A, a.ck, a.summ);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev0 && (e = cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (first)
-        col_bwd_kernel<kDB, true><<<grid, block, colb_smem<kDB>(), st>>>(C, A, Dl, Pt, w.ck, w.summ, fac, phick, segc,
-                                                                        q2, (int)n, (int)g.ld, (int)g.Ls, (int)g.P,
-                                                                        (int)g.nchunk);
+        col_bwd_kernel<kDB, true><<<grid, block, colb_smem<kDB>(), st>>>(a.probs, a.items, a.active, j, a.C, a.A, a.D,
+                                                                        a.Pt, a.ck, a.summ);
     else
-        col_bwd_kernel<kDB, false><<<grid, block, colb_smem<kDB>(), st>>>(C, A, Dl, Pt, w.ck, w.summ, fac, phick,
-                                                                         segc, q2, (int)n, (int)g.ld, (int)g.Ls,
-                                                                         (int)g.P, (int)g.nchunk);
+        col_bwd_kernel<kDB, false><<<grid, block, colb_smem<kDB>(), st>>>(a.probs, a.items, a.active, j, a.C, a.A,
+                                                                         a.D, a.Pt, a.ck, a.summ);
     e = cudaGetLastError();
     if (e == cudaSuccess && ev1) e = cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
     return e;
 }
 
-cudaError_t launch_residual(const double *Y, double *Yout, const float *Dl, const double *Ft, float *Pt, const double *d,
-                            const double *e, const unsigned long long *s_bits, int64_t n, int64_t ld,
-                            unsigned long long *rmax, bool apply_update, bool y_zero, cudaStream_t st)
+cudaError_t launch_absmax_tiles(const RefTileArgs &a, const double *F, unsigned long long *smax, cudaStream_t st)
 {
-    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
-    residual_kernel<<<grid, block, 0, st>>>(Y, Yout, Dl, Ft, Pt, d, e, s_bits, n, ld, rmax, apply_update ? 1 : 0,
-                                            y_zero ? 1 : 0);
+    absmax_tiles_kernel<<<(unsigned)a.ntiles, dim3(32, 8), 0, st>>>(a.probs, a.tiles, F, smax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_scale_in(const double *F, double *Ft, float *Pt, const double *sc, int64_t n, int64_t ld,
-                                   const unsigned long long *s_bits, cudaStream_t st)
+cudaError_t launch_scale_in_tiles(const RefTileArgs &a, const double *F, double *Ft, float *Pt,
+                                  const unsigned long long *smax, cudaStream_t st)
 {
-    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
-    refine_scale_in_kernel<<<grid, block, 0, st>>>(F, Ft, Pt, sc, n, ld, s_bits);
+    scale_in_tiles_kernel<<<(unsigned)a.ntiles, dim3(32, 8), 0, st>>>(a.probs, a.tiles, F, Ft, Pt, smax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_absmax_scaled(const double *F, const double *sc, int64_t n, unsigned long long *out,
-                                 cudaStream_t st)
+cudaError_t launch_residual_tiles(const RefTileArgs &a, const double *Y, double *Yout, const float *Dl,
+                                  const double *Ft, float *Pt, const unsigned long long *smax,
+                                  unsigned long long *rmax, const int *pair_active, bool y_zero, cudaStream_t st)
 {
-    const int64_t nn = n * n;
-    int blocks = (int)((nn + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks < 1) blocks = 1;
-    absmax_kernel<<<blocks, 256, 0, st>>>(F, sc, n, out);
+    residual_tiles_kernel<<<(unsigned)a.ntiles, dim3(32, 8), 0, st>>>(a.probs, a.tiles, Y, Yout, Dl, Ft, Pt, smax,
+                                                                      rmax, pair_active, y_zero ? 1 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_factors32(const double *d, const double *e, const double *q, int J, int64_t n,
-                             const RefineGeometry &g, float4 *fac, float *phick, float4 *segc, cudaStream_t st)
+cudaError_t launch_scale_out_tiles(const RefTileArgs &a, const double *Y, double *X, cudaStream_t st)
 {
-    const int threads = 2 * J;
-    factor32_kernel<<<(threads + 127) / 128, 128, 0, st>>>(d, e, q, J, n, (int)g.Ls, (int)g.P, (int)g.nchunk, fac,
-                                                          phick, segc);
+    scale_out_tiles_kernel<<<(unsigned)a.ntiles, dim3(32, 8), 0, st>>>(a.probs, a.tiles, Y, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factors32(const FactorJob *jobs, int njobs, cudaStream_t st)
+{
+    const int threads = 2 * njobs;
+    factor32_kernel<<<(threads + 127) / 128, 128, 0, st>>>(jobs, njobs);
     return cudaGetLastError();
 }
 

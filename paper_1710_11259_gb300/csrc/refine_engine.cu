@@ -1,0 +1,451 @@
+// Host side of the FP32-sweep / FP64-refinement solve (one problem or a batch).
+//
+// Refinement loop (per solve):
+//   smax_pr = max |F~| per (problem, rhs) pair; F~ = D_s F D_s; rho_0 = F~ / smax
+//   round r: inner ADI (one CUDA graph per tolerance level, all problems in every
+//            launch) gives the FP32 correction D; the FP64 residual kernel applies
+//            Y += smax D, forms R~ = F~ - A~Y - YA~ and the next rho; pairs with
+//            max|R~| <= tol smax stop (their iterate is carried unchanged).
+//   X = D_s Y D_s.
+// The inner tolerance of a round is the coarsest level that still gains ten times
+// what the worst active pair is missing; the first round uses the finest level
+// (1e-7, the accuracy an FP32 inner solve can deliver).
+#include "refine_engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "../../include/fps.h"
+#include "host_math.h"
+
+namespace fps {
+
+namespace {
+double bits_to_double(unsigned long long b)
+{
+    double d;
+    std::memcpy(&d, &b, sizeof(d));
+    return d;
+}
+const double kLevelTols[] = {1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2};
+}  // namespace
+
+template <typename T>
+cudaError_t RefineEngine::dalloc(T **p, size_t count)
+{
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) {
+        bytes += (int64_t)(sizeof(T) * count);
+        allocs_.push_back((void *)*p);
+    }
+    return e;
+}
+
+void RefineEngine::release()
+{
+    for (auto &L : levels_) {
+        for (cudaEvent_t e : L.ev) cudaEventDestroy(e);
+        if (L.graph) cudaGraphExecDestroy(L.graph);
+    }
+    levels_.clear();
+    for (void *p : allocs_) cudaFree(p);
+    allocs_.clear();
+    if (h_active_) cudaFreeHost(h_active_);
+    if (h_pair_active_) cudaFreeHost(h_pair_active_);
+    if (h_smax_) cudaFreeHost(h_smax_);
+    if (h_rmax_) cudaFreeHost(h_rmax_);
+    h_active_ = h_pair_active_ = nullptr;
+    h_smax_ = h_rmax_ = nullptr;
+}
+
+#define ENG_CK(call)                                                                                     \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                                    \
+            return FPS_ERR_CUDA;                                                                         \
+        }                                                                                                \
+    } while (0)
+
+int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, cudaStream_t setup_stream,
+                         int target_ctas, std::string &err)
+{
+    ns_ = ns;
+    nrhs_ = nrhs;
+    tol_ = tol;
+    cap_ = setup_stream;
+    const int np = (int)ns.size();
+    if (target_ctas <= 0) target_ctas = 8 * 152;
+    int64_t nmax = 0;
+    for (int64_t n : ns) nmax = std::max(nmax, n);
+    // every problem aims at segments of about the same length as the largest one
+    const RefineGeometry gmax = refine_geometry(nmax, target_ctas);
+    geo_.resize(np);
+    off64_.resize(np);
+    off32_.resize(np);
+    offck_.resize(np);
+    offsm_.resize(np);
+    tot64 = tot32 = totck = totsm = 0;
+    int64_t totband = 0;
+    for (int p = 0; p < np; ++p) {
+        const int64_t n = ns[p];
+        const int64_t nblk = (n + 31) / 32;
+        const int64_t m0 = (n + 1) / 2;
+        const int64_t want_seg = std::max<int64_t>(1, (m0 + gmax.Ls - 1) / gmax.Ls);
+        geo_[p] = refine_geometry(n, (int)std::min<int64_t>(nblk * want_seg, 1 << 30));
+        off64_[p] = tot64;
+        off32_[p] = tot32;
+        offck_[p] = totck;
+        offsm_[p] = totsm;
+        tot64 += (int64_t)nrhs * n * n;
+        tot32 += (int64_t)nrhs * n * geo_[p].ld;
+        totck += (int64_t)nrhs * refine_checkpoint_floats(geo_[p]);
+        totsm += (int64_t)nrhs * refine_summary_float2(geo_[p]);
+        totband += 3 * n;
+    }
+    npairs_ = np * nrhs;
+
+    ENG_CK(refine_setup_kernels());
+    ENG_CK(dalloc(&Ft_, (size_t)tot64));
+    ENG_CK(dalloc(&Y0_, (size_t)tot64));
+    ENG_CK(dalloc(&Y1_, (size_t)tot64));
+    ENG_CK(dalloc(&bands_, (size_t)totband));
+    ENG_CK(dalloc(&Pt_, (size_t)tot32));
+    ENG_CK(dalloc(&A_, (size_t)tot32));
+    ENG_CK(dalloc(&C_, (size_t)tot32));
+    ENG_CK(dalloc(&D_, (size_t)tot32));
+    ENG_CK(dalloc(&ck_, (size_t)totck));
+    ENG_CK(dalloc(&summ_, (size_t)totsm));
+    ENG_CK(dalloc(&d_active_, (size_t)np));
+    ENG_CK(dalloc(&d_pair_active_, (size_t)npairs_));
+    ENG_CK(dalloc(&d_smax_, (size_t)npairs_));
+    ENG_CK(dalloc(&d_rmax_, (size_t)npairs_));
+    ENG_CK(cudaMallocHost((void **)&h_active_, sizeof(int) * np));
+    ENG_CK(cudaMallocHost((void **)&h_pair_active_, sizeof(int) * npairs_));
+    ENG_CK(cudaMallocHost((void **)&h_smax_, sizeof(unsigned long long) * npairs_));
+    ENG_CK(cudaMallocHost((void **)&h_rmax_, sizeof(unsigned long long) * npairs_));
+    float *f32bufs[] = {Pt_, A_, C_, D_};
+    for (float *b : f32bufs) ENG_CK(cudaMemsetAsync(b, 0, sizeof(float) * (size_t)tot32, cap_));
+
+    // bands (d, e zero-padded, 1/sqrt(E)) and the FP64 tile table
+    std::vector<double> hband((size_t)totband);
+    std::vector<RefProb64> p64(np);
+    std::vector<int4> tiles;
+    {
+        int64_t ob = 0;
+        std::vector<double> d, e, s;
+        for (int p = 0; p < np; ++p) {
+            const int64_t n = ns[p];
+            square_bands(n, d, e);
+            inv_sqrt_E(n, s);
+            std::copy(d.begin(), d.end(), hband.begin() + ob);
+            std::copy(e.begin(), e.end(), hband.begin() + ob + n);
+            std::copy(s.begin(), s.end(), hband.begin() + ob + 2 * n);
+            RefProb64 &q = p64[p];
+            q.n = (int)n;
+            q.ld = (int)geo_[p].ld;
+            q.off64 = off64_[p];
+            q.off32 = off32_[p];
+            q.rhs32 = n * geo_[p].ld;
+            q.d = bands_ + ob;
+            q.e = bands_ + ob + n;
+            q.s = bands_ + ob + 2 * n;
+            q.pair0 = p * nrhs;
+            ob += 3 * n;
+            const int nt = (int)((n + 31) / 32);
+            for (int r = 0; r < nrhs; ++r)
+                for (int ty = 0; ty < nt; ++ty)
+                    for (int tx = 0; tx < nt; ++tx) tiles.push_back(make_int4(p * 256 + r, tx, ty, 0));
+        }
+    }
+    ntiles_ = (int64_t)tiles.size();
+    ENG_CK(dalloc(&d_p64_, (size_t)np));
+    ENG_CK(dalloc(&d_tiles_, (size_t)ntiles_));
+    ENG_CK(cudaMemcpyAsync(bands_, hband.data(), sizeof(double) * totband, cudaMemcpyHostToDevice, cap_));
+    ENG_CK(cudaMemcpyAsync(d_p64_, p64.data(), sizeof(RefProb64) * np, cudaMemcpyHostToDevice, cap_));
+    ENG_CK(cudaMemcpyAsync(d_tiles_, tiles.data(), sizeof(int4) * ntiles_, cudaMemcpyHostToDevice, cap_));
+
+    // work items of the passes: largest problems first
+    std::vector<int> order(np);
+    for (int p = 0; p < np; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
+    std::vector<int4> items;
+    for (int p : order)
+        for (int r = 0; r < nrhs; ++r)
+            for (int64_t b = 0; b < geo_[p].nblk; ++b)
+                for (int64_t sg = 0; sg < geo_[p].P; ++sg) items.push_back(make_int4(p, r, (int)b, (int)sg));
+    nitems_ = (int64_t)items.size();
+    ENG_CK(dalloc(&d_items_, (size_t)nitems_));
+    ENG_CK(cudaMemcpyAsync(d_items_, items.data(), sizeof(int4) * nitems_, cudaMemcpyHostToDevice, cap_));
+
+    // tolerance levels: shifts per problem, factor tables via factor jobs
+    for (double lt : kLevelTols) {
+        Level L;
+        L.tol = lt;
+        L.J.resize(np);
+        int64_t nfac = 0, nph = 0, nsc = 0, nq = 0;
+        for (int p = 0; p < np; ++p) {
+            const double eps = square_eps(ns[p]);
+            L.J[p] = adi_iterations(-1.0, -eps, eps, 1.0, lt);
+            L.Jmax = std::max(L.Jmax, L.J[p]);
+            nfac += (int64_t)L.J[p] * ns[p];
+            nph += (int64_t)L.J[p] * 2 * geo_[p].nchunk;
+            nsc += (int64_t)L.J[p] * 2 * geo_[p].P;
+            nq += L.J[p];
+        }
+        ENG_CK(dalloc(&L.fac, (size_t)nfac));
+        ENG_CK(dalloc(&L.phick, (size_t)nph));
+        ENG_CK(dalloc(&L.segc, (size_t)nsc));
+        ENG_CK(dalloc(&L.q2, (size_t)nq));
+        ENG_CK(dalloc(&L.d_probs, (size_t)np));
+        ENG_CK(dalloc(&L.d_jobs, (size_t)nq));
+        std::vector<RefProb> probs(np);
+        std::vector<FactorJob> jobs;
+        std::vector<float> q2h;
+        jobs.reserve(nq);
+        q2h.reserve(nq);
+        int64_t of = 0, oph = 0, osc = 0, oq = 0;
+        std::vector<double> q;
+        for (int p = 0; p < np; ++p) {
+            const int64_t n = ns[p];
+            const RefineGeometry &g = geo_[p];
+            zolotarev_shifts_symmetric(square_eps(n), 1.0, L.J[p], q);
+            RefProb &rp = probs[p];
+            rp.n = (int)n;
+            rp.ld = (int)g.ld;
+            rp.Ls = (int)g.Ls;
+            rp.P = (int)g.P;
+            rp.nchunk = (int)g.nchunk;
+            rp.J = L.J[p];
+            rp.off32 = off32_[p];
+            rp.rhs32 = n * g.ld;
+            rp.offck = offck_[p];
+            rp.rhsck = refine_checkpoint_floats(g);
+            rp.offsm = offsm_[p];
+            rp.rhssm = refine_summary_float2(g);
+            rp.fac = L.fac + of;
+            rp.phick = L.phick + oph;
+            rp.segc = L.segc + osc;
+            rp.q2 = L.q2 + oq;
+            for (int j = 0; j < L.J[p]; ++j) {
+                FactorJob jb;
+                jb.q = q[j];
+                jb.n = n;
+                jb.Ls = g.Ls;
+                jb.P = g.P;
+                jb.nchunk = g.nchunk;
+                jb.d = p64[p].d;
+                jb.e = p64[p].e;
+                jb.fac = L.fac + of + (int64_t)j * n;
+                jb.phick = L.phick + oph + (int64_t)j * 2 * g.nchunk;
+                jb.segc = L.segc + osc + (int64_t)j * 2 * g.P;
+                jobs.push_back(jb);
+                q2h.push_back((float)(2.0 * q[j]));
+            }
+            of += (int64_t)L.J[p] * n;
+            oph += (int64_t)L.J[p] * 2 * g.nchunk;
+            osc += (int64_t)L.J[p] * 2 * g.P;
+            oq += L.J[p];
+        }
+        ENG_CK(cudaMemcpyAsync(L.d_probs, probs.data(), sizeof(RefProb) * np, cudaMemcpyHostToDevice, cap_));
+        ENG_CK(cudaMemcpyAsync(L.d_jobs, jobs.data(), sizeof(FactorJob) * jobs.size(), cudaMemcpyHostToDevice, cap_));
+        ENG_CK(cudaMemcpyAsync(L.q2, q2h.data(), sizeof(float) * q2h.size(), cudaMemcpyHostToDevice, cap_));
+        ENG_CK(launch_factors32(L.d_jobs, (int)jobs.size(), cap_));
+        // the host vectors must outlive the asynchronous copies
+        ENG_CK(cudaStreamSynchronize(cap_));
+        levels_.push_back(std::move(L));
+    }
+    {
+        int big = 0;
+        for (int p = 0; p < np; ++p)
+            if (ns[p] > ns[big]) big = p;
+        J_inner_first = levels_[0].J[big];
+    }
+    for (auto &L : levels_) {
+        int st = build_graph(L, err);
+        if (st != FPS_OK) return st;
+    }
+    return FPS_OK;
+}
+
+int RefineEngine::build_graph(Level &L, std::string &err)
+{
+    if (L.graph) {
+        cudaGraphExecDestroy(L.graph);
+        L.graph = nullptr;
+    }
+    RefPassArgs a;
+    a.probs = L.d_probs;
+    a.items = d_items_;
+    a.nitems = nitems_;
+    a.active = d_active_;
+    a.Pt = Pt_;
+    a.A = A_;
+    a.C = C_;
+    a.D = D_;
+    a.ck = ck_;
+    a.summ = summ_;
+    ENG_CK(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    const bool ins = instrument_ && (int)L.ev.size() == 2 * L.Jmax;
+    for (int j = 0; j < L.Jmax && e == cudaSuccess; ++j) {
+        e = launch_row_pass(a, j, cap_);
+        if (e == cudaSuccess)
+            e = launch_col_pass(a, j, j == 0, cap_, ins ? L.ev[2 * j] : nullptr, ins ? L.ev[2 * j + 1] : nullptr);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap_, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        err = std::string("refine graph capture: ") + cudaGetErrorString(e);
+        return FPS_ERR_CUDA;
+    }
+    ENG_CK(e2);
+    e = cudaGraphInstantiate(&L.graph, g, 0);
+    cudaGraphDestroy(g);
+    ENG_CK(e);
+    return FPS_OK;
+}
+
+int RefineEngine::solve(const double *F, double *X, cudaStream_t st, std::string &err)
+{
+    const int np = (int)ns_.size();
+    RefTileArgs ta;
+    ta.probs = d_p64_;
+    ta.tiles = d_tiles_;
+    ta.ntiles = ntiles_;
+    launches_last = 0;
+    levels_used_.clear();
+
+    ENG_CK(cudaMemsetAsync(d_smax_, 0, sizeof(unsigned long long) * npairs_, st));
+    ENG_CK(launch_absmax_tiles(ta, F, d_smax_, st));
+    ENG_CK(cudaMemcpyAsync(h_smax_, d_smax_, sizeof(unsigned long long) * npairs_, cudaMemcpyDeviceToHost, st));
+    ENG_CK(cudaStreamSynchronize(st));
+    launches_last += 1;
+    std::vector<double> sF(npairs_);
+    for (int k = 0; k < npairs_; ++k) {
+        sF[k] = bits_to_double(h_smax_[k]);
+        if (!std::isfinite(sF[k])) {
+            err = "F holds NaN or Inf";
+            return FPS_ERR_NONFINITE;
+        }
+        h_pair_active_[k] = sF[k] > 0.0 ? 1 : 0;  // an all-zero right-hand side is already solved (X = 0)
+    }
+    for (int p = 0; p < np; ++p) {
+        h_active_[p] = 0;
+        for (int r = 0; r < nrhs_; ++r) h_active_[p] |= h_pair_active_[p * nrhs_ + r];
+    }
+    ENG_CK(cudaMemcpyAsync(d_active_, h_active_, sizeof(int) * np, cudaMemcpyHostToDevice, st));
+    ENG_CK(cudaMemcpyAsync(d_pair_active_, h_pair_active_, sizeof(int) * npairs_, cudaMemcpyHostToDevice, st));
+    ENG_CK(launch_scale_in_tiles(ta, F, Ft_, Pt_, d_smax_, st));
+    launches_last += 1;
+
+    std::vector<double> rel(npairs_, 0.0);
+    for (int k = 0; k < npairs_; ++k) rel[k] = h_pair_active_[k] ? 1.0 : 0.0;
+    double *Ycur = Y0_, *Ynext = Y1_;
+    bool any_active = false;
+    for (int k = 0; k < npairs_; ++k) any_active = any_active || h_pair_active_[k];
+    int round = 0;
+    bool converged = !any_active;
+    for (; round < max_rounds && !converged; ++round) {
+        double worst = 0.0;
+        for (int k = 0; k < npairs_; ++k)
+            if (h_pair_active_[k]) worst = std::max(worst, rel[k]);
+        const double want = 0.1 * tol_ / worst;
+        size_t li = 0;
+        for (size_t l = 0; l < levels_.size(); ++l)
+            if (levels_[l].tol <= want) li = l;
+        if (round == 0) li = 0;
+        ENG_CK(cudaGraphLaunch(levels_[li].graph, st));
+        levels_used_.push_back((int)li);
+        launches_last += 4LL * levels_[li].Jmax;
+        ENG_CK(cudaMemsetAsync(d_rmax_, 0, sizeof(unsigned long long) * npairs_, st));
+        ENG_CK(launch_residual_tiles(ta, Ycur, Ynext, D_, Ft_, Pt_, d_smax_, d_rmax_, d_pair_active_, round == 0, st));
+        launches_last += 1;
+        ENG_CK(cudaMemcpyAsync(h_rmax_, d_rmax_, sizeof(unsigned long long) * npairs_, cudaMemcpyDeviceToHost, st));
+        ENG_CK(cudaStreamSynchronize(st));
+        std::swap(Ycur, Ynext);
+        converged = true;
+        for (int k = 0; k < npairs_; ++k) {
+            if (!h_pair_active_[k]) continue;
+            const double r = bits_to_double(h_rmax_[k]) / sF[k];
+            if (!std::isfinite(r)) {
+                err = "non-finite residual";
+                return FPS_ERR_NONFINITE;
+            }
+            rel[k] = r;
+            if (r <= tol_) h_pair_active_[k] = 0;
+            else converged = false;
+        }
+        for (int p = 0; p < np; ++p) {
+            h_active_[p] = 0;
+            for (int r = 0; r < nrhs_; ++r) h_active_[p] |= h_pair_active_[p * nrhs_ + r];
+        }
+        ENG_CK(cudaMemcpyAsync(d_active_, h_active_, sizeof(int) * np, cudaMemcpyHostToDevice, st));
+        ENG_CK(cudaMemcpyAsync(d_pair_active_, h_pair_active_, sizeof(int) * npairs_, cudaMemcpyHostToDevice, st));
+    }
+    rounds_last = round;
+    resid_last = 0.0;
+    for (int k = 0; k < npairs_; ++k) resid_last = std::max(resid_last, rel[k]);
+    if (round == 0) {
+        // every right-hand side was zero
+        ENG_CK(cudaMemsetAsync(X, 0, sizeof(double) * tot64, st));
+        return FPS_OK;
+    }
+    ENG_CK(launch_scale_out_tiles(ta, Ycur, X, st));
+    launches_last += 1;
+    if (!converged) {
+        err = "refinement did not reach tol";
+        return FPS_ERR_NOT_CONVERGED;
+    }
+    return FPS_OK;
+}
+
+int RefineEngine::set_instrument(bool on, std::string &err)
+{
+    instrument_ = on;
+    for (auto &L : levels_) {
+        for (cudaEvent_t e : L.ev) cudaEventDestroy(e);
+        L.ev.clear();
+        if (on) {
+            L.ev.resize(2 * (size_t)L.Jmax);
+            for (auto &e : L.ev) ENG_CK(cudaEventCreate(&e));
+        }
+        int st = build_graph(L, err);
+        if (st != FPS_OK) return st;
+    }
+    return FPS_OK;
+}
+
+int RefineEngine::kernel_times(int *count, double *total_ms, double *alg_bytes, std::string &err)
+{
+    double elems = 0.0;
+    for (size_t p = 0; p < ns_.size(); ++p) elems += (double)nrhs_ * (double)ns_[p] * (double)ns_[p];
+    int c = 0;
+    double ms = 0.0, by = 0.0;
+    std::vector<int> seen;
+    for (int li : levels_used_) {
+        if (std::find(seen.begin(), seen.end(), li) != seen.end()) continue;
+        seen.push_back(li);
+        const Level &L = levels_[li];
+        for (int j = 0; j < L.Jmax; ++j) {
+            float t = 0.f;
+            ENG_CK(cudaEventElapsedTime(&t, L.ev[2 * j], L.ev[2 * j + 1]));
+            ms += t;
+            ++c;
+            // elements of the problems that run iteration j: c, a (, D) read; rho+, D written
+            double ej = 0.0;
+            for (size_t p = 0; p < ns_.size(); ++p)
+                if (j < L.J[p]) ej += (double)nrhs_ * (double)ns_[p] * (double)ns_[p];
+            by += (j == 0 ? 4.0 : 5.0) * 4.0 * ej;
+        }
+    }
+    (void)elems;
+    *count = c;
+    *total_ms = ms;
+    *alg_bytes = by;
+    return FPS_OK;
+}
+
+}  // namespace fps
