@@ -71,6 +71,8 @@ typedef struct {
     double tol;             /* requested tolerance */
     int64_t device_bytes;   /* device memory owned by the plan */
     int64_t kernel_launches; /* kernels of this library launched by the last solve */
+    int pass_ctas;          /* FP32_REFINE: CTAs per pass aimed at on the largest problem
+                               (picked by the autotuner unless FPS_AUTOTUNE=0) */
 } fps_plan_info_t;
 
 /*

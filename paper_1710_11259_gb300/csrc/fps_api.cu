@@ -420,6 +420,7 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->tol = plan->tol;
     info->device_bytes = plan->bytes;
     info->kernel_launches = plan->launches_last;
+    info->pass_ctas = plan->eng ? plan->eng->chosen_target_ctas : 0;
     return FPS_OK;
 }
 

@@ -14,7 +14,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
+
+#include <sys/stat.h>
 
 #include "../../include/fps.h"
 #include "host_math.h"
@@ -68,6 +74,23 @@ void RefineEngine::release()
         }                                                                                                \
     } while (0)
 
+// Per-problem geometry for a pass size of about `target_ctas` CTAs on the largest
+// problem: every problem uses segments of about the same length as the largest.
+static void batch_geometry(const std::vector<int64_t> &ns, int target_ctas, std::vector<RefineGeometry> &geo)
+{
+    int64_t nmax = 0;
+    for (int64_t n : ns) nmax = std::max(nmax, n);
+    const RefineGeometry gmax = refine_geometry(nmax, target_ctas);
+    geo.resize(ns.size());
+    for (size_t p = 0; p < ns.size(); ++p) {
+        const int64_t n = ns[p];
+        const int64_t nblk = (n + 31) / 32;
+        const int64_t m0 = (n + 1) / 2;
+        const int64_t want_seg = std::max<int64_t>(1, (m0 + gmax.Ls - 1) / gmax.Ls);
+        geo[p] = refine_geometry(n, (int)std::min<int64_t>(nblk * want_seg, 1 << 30));
+    }
+}
+
 int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, cudaStream_t setup_stream,
                          int target_ctas, std::string &err)
 {
@@ -76,12 +99,22 @@ int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, c
     tol_ = tol;
     cap_ = setup_stream;
     const int np = (int)ns.size();
-    if (target_ctas <= 0) target_ctas = 8 * 152;
-    int64_t nmax = 0;
-    for (int64_t n : ns) nmax = std::max(nmax, n);
-    // every problem aims at segments of about the same length as the largest one
-    const RefineGeometry gmax = refine_geometry(nmax, target_ctas);
-    geo_.resize(np);
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // candidate pass sizes (CTAs on the largest problem) for the autotuner
+    const int cand[] = {4 * sms, 8 * sms, 16 * sms, 32 * sms};
+    const int ncand = 4;
+    int64_t sm_cap = 0;  // summary storage large enough for every candidate
+    {
+        std::vector<RefineGeometry> g;
+        for (int c = 0; c < ncand; ++c) {
+            batch_geometry(ns, cand[c], g);
+            int64_t t = 0;
+            for (int p = 0; p < np; ++p) t += (int64_t)nrhs * refine_summary_float2(g[p]);
+            sm_cap = std::max(sm_cap, t);
+        }
+    }
+    batch_geometry(ns, target_ctas > 0 ? target_ctas : 8 * sms, geo_);
     off64_.resize(np);
     off32_.resize(np);
     offck_.resize(np);
@@ -90,20 +123,15 @@ int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, c
     int64_t totband = 0;
     for (int p = 0; p < np; ++p) {
         const int64_t n = ns[p];
-        const int64_t nblk = (n + 31) / 32;
-        const int64_t m0 = (n + 1) / 2;
-        const int64_t want_seg = std::max<int64_t>(1, (m0 + gmax.Ls - 1) / gmax.Ls);
-        geo_[p] = refine_geometry(n, (int)std::min<int64_t>(nblk * want_seg, 1 << 30));
         off64_[p] = tot64;
         off32_[p] = tot32;
         offck_[p] = totck;
-        offsm_[p] = totsm;
         tot64 += (int64_t)nrhs * n * n;
         tot32 += (int64_t)nrhs * n * geo_[p].ld;
         totck += (int64_t)nrhs * refine_checkpoint_floats(geo_[p]);
-        totsm += (int64_t)nrhs * refine_summary_float2(geo_[p]);
         totband += 3 * n;
     }
+    totsm = sm_cap;
     npairs_ = np * nrhs;
 
     ENG_CK(refine_setup_kernels());
@@ -165,6 +193,23 @@ int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, c
     ENG_CK(cudaMemcpyAsync(bands_, hband.data(), sizeof(double) * totband, cudaMemcpyHostToDevice, cap_));
     ENG_CK(cudaMemcpyAsync(d_p64_, p64.data(), sizeof(RefProb64) * np, cudaMemcpyHostToDevice, cap_));
     ENG_CK(cudaMemcpyAsync(d_tiles_, tiles.data(), sizeof(int4) * ntiles_, cudaMemcpyHostToDevice, cap_));
+
+    // pass sizes: autotune (or the caller's choice), then the summary offsets
+    if (target_ctas <= 0) {
+        int best = -1;
+        const int st = autotune(cand, ncand, p64, best, err);
+        if (st != FPS_OK) return st;
+        target_ctas = best;
+    }
+    chosen_target_ctas = target_ctas;
+    batch_geometry(ns, target_ctas, geo_);
+    {
+        int64_t o = 0;
+        for (int p = 0; p < np; ++p) {
+            offsm_[p] = o;
+            o += (int64_t)nrhs * refine_summary_float2(geo_[p]);
+        }
+    }
 
     // work items of the passes: largest problems first
     std::vector<int> order(np);
@@ -265,6 +310,202 @@ int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, c
     for (auto &L : levels_) {
         int st = build_graph(L, err);
         if (st != FPS_OK) return st;
+    }
+    return FPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the pass size.  Each candidate (CTAs per pass on the largest
+// problem, which fixes every problem's segment length) gets its own segment
+// tables for the first two shifts of the finest level; two inner iterations
+// (row and column passes) are timed with CUDA events on the plan's own buffers
+// and the fastest candidate is kept.  Results are cached per (GPU name, nrhs,
+// size list) in $FPS_AUTOTUNE_CACHE (default ~/.cache/fps_gb300_autotune.txt);
+// FPS_AUTOTUNE=0 skips tuning and uses 8 CTAs per SM.
+// ---------------------------------------------------------------------------
+static std::string tune_key(const std::vector<int64_t> &ns, int nrhs)
+{
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    uint64_t h = 1469598103934665603ULL;  // FNV-1a over the sizes
+    for (int64_t n : ns) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (uint64_t)((n >> (8 * b)) & 0xff);
+            h *= 1099511628211ULL;
+        }
+    }
+    std::ostringstream os;
+    os << name << "|" << nrhs << "|" << ns.size() << "|" << std::hex << h;
+    return os.str();
+}
+
+static std::string tune_cache_path()
+{
+    const char *p = std::getenv("FPS_AUTOTUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = std::getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/fps_gb300_autotune.txt";
+}
+
+int RefineEngine::autotune(const int *cand, int ncand, const std::vector<RefProb64> &p64, int &best,
+                           std::string &err)
+{
+    const char *env = std::getenv("FPS_AUTOTUNE");
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    best = 8 * sms;
+    if (env && std::string(env) == "0") return FPS_OK;
+    const std::string key = tune_key(ns_, nrhs_);
+    const std::string path = tune_cache_path();
+    {
+        std::ifstream in(path);
+        std::string k;
+        int v;
+        while (in >> k >> v)
+            if (k == key) {
+                best = v;
+                return FPS_OK;
+            }
+    }
+    const int np = (int)ns_.size();
+    float best_ms = 3.4e38f;
+    tune_ms.clear();
+    for (int c = 0; c < ncand; ++c) {
+        std::vector<RefineGeometry> g;
+        batch_geometry(ns_, cand[c], g);
+        std::vector<RefProb> probs(np);
+        std::vector<FactorJob> jobs;
+        std::vector<float> q2h;
+        std::vector<int4> items;
+        int64_t nfac = 0, nph = 0, nsc = 0, osm = 0;
+        std::vector<int> Jt(np);
+        for (int p = 0; p < np; ++p) {
+            const double eps = square_eps(ns_[p]);
+            Jt[p] = std::min(2, adi_iterations(-1.0, -eps, eps, 1.0, kLevelTols[0]));
+            nfac += (int64_t)Jt[p] * ns_[p];
+            nph += (int64_t)Jt[p] * 2 * g[p].nchunk;
+            nsc += (int64_t)Jt[p] * 2 * g[p].P;
+        }
+        float4 *fac = nullptr, *segc = nullptr;
+        float *phick = nullptr, *q2 = nullptr;
+        RefProb *dprobs = nullptr;
+        FactorJob *djobs = nullptr;
+        int4 *ditems = nullptr;
+        auto cleanup = [&]() {
+            void *ps[] = {fac, segc, phick, q2, dprobs, djobs, ditems};
+            for (void *q : ps)
+                if (q) cudaFree(q);
+        };
+#define TUNE_CK(call)                                                                                        do {                                                                                                         cudaError_t e_ = (call);                                                                                 if (e_ != cudaSuccess) {                                                                                     cleanup();                                                                                               err = std::string("autotune: ") + #call + ": " + cudaGetErrorString(e_);                                 return FPS_ERR_CUDA;                                                                                 }                                                                                                    } while (0)
+        TUNE_CK(cudaMalloc((void **)&fac, sizeof(float4) * nfac));
+        TUNE_CK(cudaMalloc((void **)&phick, sizeof(float) * nph));
+        TUNE_CK(cudaMalloc((void **)&segc, sizeof(float4) * nsc));
+        TUNE_CK(cudaMalloc((void **)&q2, sizeof(float) * 2 * np));
+        TUNE_CK(cudaMalloc((void **)&dprobs, sizeof(RefProb) * np));
+        TUNE_CK(cudaMalloc((void **)&djobs, sizeof(FactorJob) * 2 * np));
+        int64_t of = 0, oph = 0, osc = 0;
+        std::vector<double> q;
+        for (int p = 0; p < np; ++p) {
+            const int64_t n = ns_[p];
+            zolotarev_shifts_symmetric(square_eps(n), 1.0, Jt[p], q);
+            RefProb &rp = probs[p];
+            rp.n = (int)n;
+            rp.ld = (int)g[p].ld;
+            rp.Ls = (int)g[p].Ls;
+            rp.P = (int)g[p].P;
+            rp.nchunk = (int)g[p].nchunk;
+            rp.J = Jt[p];
+            rp.off32 = off32_[p];
+            rp.rhs32 = n * g[p].ld;
+            rp.offck = offck_[p];
+            rp.rhsck = refine_checkpoint_floats(g[p]);
+            rp.offsm = osm;
+            rp.rhssm = refine_summary_float2(g[p]);
+            rp.fac = fac + of;
+            rp.phick = phick + oph;
+            rp.segc = segc + osc;
+            rp.q2 = q2 + 2 * p;
+            osm += (int64_t)nrhs_ * rp.rhssm;
+            for (int j = 0; j < Jt[p]; ++j) {
+                FactorJob jb;
+                jb.q = q[j];
+                jb.n = n;
+                jb.Ls = g[p].Ls;
+                jb.P = g[p].P;
+                jb.nchunk = g[p].nchunk;
+                jb.d = p64[p].d;
+                jb.e = p64[p].e;
+                jb.fac = fac + of + (int64_t)j * n;
+                jb.phick = phick + oph + (int64_t)j * 2 * g[p].nchunk;
+                jb.segc = segc + osc + (int64_t)j * 2 * g[p].P;
+                jobs.push_back(jb);
+            }
+            q2h.push_back((float)(2.0 * q[0]));
+            q2h.push_back((float)(2.0 * q[Jt[p] > 1 ? 1 : 0]));
+            of += (int64_t)Jt[p] * n;
+            oph += (int64_t)Jt[p] * 2 * g[p].nchunk;
+            osc += (int64_t)Jt[p] * 2 * g[p].P;
+            for (int r = 0; r < nrhs_; ++r)
+                for (int64_t b = 0; b < g[p].nblk; ++b)
+                    for (int64_t sg = 0; sg < g[p].P; ++sg) items.push_back(make_int4(p, r, (int)b, (int)sg));
+        }
+        TUNE_CK(cudaMalloc((void **)&ditems, sizeof(int4) * items.size()));
+        TUNE_CK(cudaMemcpyAsync(dprobs, probs.data(), sizeof(RefProb) * np, cudaMemcpyHostToDevice, cap_));
+        TUNE_CK(cudaMemcpyAsync(djobs, jobs.data(), sizeof(FactorJob) * jobs.size(), cudaMemcpyHostToDevice, cap_));
+        TUNE_CK(cudaMemcpyAsync(q2, q2h.data(), sizeof(float) * q2h.size(), cudaMemcpyHostToDevice, cap_));
+        TUNE_CK(cudaMemcpyAsync(ditems, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, cap_));
+        TUNE_CK(launch_factors32(djobs, (int)jobs.size(), cap_));
+        TUNE_CK(cudaMemsetAsync(d_active_, 0xff, sizeof(int) * np, cap_));  // all problems active (non-zero)
+        RefPassArgs a;
+        a.probs = dprobs;
+        a.items = ditems;
+        a.nitems = (int64_t)items.size();
+        a.active = d_active_;
+        a.Pt = Pt_;
+        a.A = A_;
+        a.C = C_;
+        a.D = D_;
+        a.ck = ck_;
+        a.summ = summ_;
+        cudaEvent_t e0, e1;
+        TUNE_CK(cudaEventCreate(&e0));
+        TUNE_CK(cudaEventCreate(&e1));
+        // warm-up iteration, then two timed iterations
+        TUNE_CK(launch_row_pass(a, 0, cap_));
+        TUNE_CK(launch_col_pass(a, 0, true, cap_));
+        TUNE_CK(cudaEventRecord(e0, cap_));
+        for (int j = 0; j < 2; ++j) {
+            TUNE_CK(launch_row_pass(a, j, cap_));
+            TUNE_CK(launch_col_pass(a, j, j == 0, cap_));
+        }
+        TUNE_CK(cudaEventRecord(e1, cap_));
+        TUNE_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TUNE_CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cleanup();
+#undef TUNE_CK
+        tune_ms.push_back(ms);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    // restore the zero state of the FP32 arrays the timing runs wrote
+    float *f32bufs[] = {Pt_, A_, C_, D_};
+    for (float *b : f32bufs) ENG_CK(cudaMemsetAsync(b, 0, sizeof(float) * (size_t)tot32, cap_));
+    ENG_CK(cudaStreamSynchronize(cap_));
+    {
+        const size_t slash = path.find_last_of('/');
+        if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // may exist
+        std::ofstream out(path, std::ios::app);
+        if (out) out << key << " " << best << "\n";
     }
     return FPS_OK;
 }

@@ -36,6 +36,8 @@ public:
     int64_t launches_last = 0;
     int max_rounds = 8;
     int64_t total_elems() const { return tot64; }
+    int chosen_target_ctas = 0;     // pass size picked by the autotuner (or given)
+    std::vector<float> tune_ms;     // autotuner timings of the candidates (ms), if it ran
 
 private:
     struct Level {
@@ -52,6 +54,7 @@ private:
         std::vector<cudaEvent_t> ev;
     };
     int build_graph(Level &L, std::string &err);
+    int autotune(const int *cand, int ncand, const std::vector<RefProb64> &p64, int &best, std::string &err);
 
     std::vector<int64_t> ns_;
     int nrhs_ = 1;

@@ -96,3 +96,33 @@ def test_batched_workload_512_problems(api):
         r = int(p) % 4
         Xo = oracle.poisson_square(rhs[p][r], 1e-13)
         assert _relmax(Xs[p][r], Xo) <= TOL_REFINE, (ns[p], r)
+
+
+def test_autotuner_picks_and_caches(api, tmp_path, monkeypatch):
+    """The pass size is picked by timing candidates on the plan's own buffers, then cached."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("FPS_AUTOTUNE_CACHE", str(cache))
+    monkeypatch.delenv("FPS_AUTOTUNE", raising=False)
+    ns = [300, 257, 64, 33]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    plan = api.plan_create_batched(ns, nrhs=2, tol=1e-10, precision="fp32_refine")
+    chosen = api.plan_info(plan)["pass_ctas"]
+    api.plan_destroy(plan)
+    assert chosen in {4 * sms, 8 * sms, 16 * sms, 32 * sms}
+    lines = cache.read_text().split("\n")
+    assert len([ln for ln in lines if ln.strip()]) == 1
+    plan = api.plan_create_batched(ns, nrhs=2, tol=1e-10, precision="fp32_refine")
+    assert api.plan_info(plan)["pass_ctas"] == chosen
+    F = torch.from_numpy(np.concatenate([inputs.square_rhs(n, 60 + n).ravel() for n in ns for _ in range(2)])).cuda()
+    X = api.poisson_square_solve(plan, F)
+    torch.cuda.synchronize()
+    api.plan_destroy(plan)
+    assert len([ln for ln in cache.read_text().split("\n") if ln.strip()]) == 1
+    x = X.cpu().numpy()
+    f = F.cpu().numpy()
+    o = 0
+    for n in ns:
+        for _ in range(2):
+            Xo = oracle.poisson_square(f[o:o + n * n].reshape(n, n), 1e-13)
+            assert _relmax(x[o:o + n * n].reshape(n, n), Xo) <= TOL_REFINE
+            o += n * n
