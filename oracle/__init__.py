@@ -74,6 +74,9 @@ def _lib(variant: str = "double") -> ctypes.CDLL:
             lib.orc_poisson_square.restype = ctypes.c_int
             lib.orc_poisson_square_partial.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_int, c_dp, c_dp]
             lib.orc_poisson_square_partial.restype = ctypes.c_int
+            lib.orc_poisson_cube.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double, c_dp,
+                                             c_dp, ctypes.POINTER(ctypes.c_int)]
+            lib.orc_poisson_cube.restype = ctypes.c_long
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_set_num_threads.argtypes = [ctypes.c_int]
             lib.orc_real_bytes.restype = ctypes.c_int
@@ -165,6 +168,18 @@ def poisson_square_partial(F, tol: float, jmax: int) -> np.ndarray:
     X = np.zeros_like(F)
     _lib().orc_poisson_square_partial(n, tol, int(jmax), _ptr(F), _ptr(X))
     return X
+
+
+def poisson_cube(F, tol: float = 1e-13, tol_mid: float = 1e-15, tol_in: float = 1e-15, variant: str = "double"):
+    """Solve (5.2) on the cube by the nested ADI of Sec. 5.  Returns (X, J_outer, inner
+    iterations over full tensors)."""
+    F = _f64(F)
+    n = F.shape[0]
+    assert F.shape == (n, n, n)
+    X = np.zeros_like(F)
+    J = ctypes.c_int()
+    inner = _lib(variant).orc_poisson_cube(n, tol, tol_mid, tol_in, _ptr(F), _ptr(X), ctypes.byref(J))
+    return X, J.value, int(inner)
 
 
 def square_iterations(n: int, tol: float) -> int:

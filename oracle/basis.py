@@ -102,3 +102,56 @@ def monomial_coeffs(values: np.ndarray, deg: int) -> np.ndarray:
             k += 1
     assert k == len(values)
     return c
+
+
+# --------------------------------------------------------------------------
+# The cube: u = (1-x^2)(1-y^2)(1-z^2) p(x, y, z), coefficients c[a, b, g] of x^a y^b z^g.
+# Tensor index order (x, y, z): X[i, j, k] pairs C~_i(x) C~_j(y) C~_k(z).
+# --------------------------------------------------------------------------
+def project_3d(f, n: int, N: int) -> np.ndarray:
+    """F[i, j, k] = int f(x,y,z) C~_i(x) C~_j(y) C~_k(z) (1-x^2)(1-y^2)(1-z^2)."""
+    x, w = gauss_jacobi(N)
+    Bm = basis_matrix(n, x) * w                      # [j, a]
+    Xg, Yg, Zg = np.meshgrid(x, x, x, indexing="ij")
+    vals = f(Xg, Yg, Zg)
+    return np.einsum("ia,jb,kc,abc->ijk", Bm, Bm, Bm, vals)
+
+
+def _poly3_eval(c, X, Y, Z):
+    out = np.zeros_like(X)
+    for a in range(c.shape[0]):
+        for b in range(c.shape[1]):
+            for g in range(c.shape[2]):
+                if c[a, b, g] != 0.0:
+                    out += c[a, b, g] * X**a * Y**b * Z**g
+    return out
+
+
+def _poly3_bubble(c):
+    bub = np.array([1.0, 0.0, -1.0])
+    out = np.zeros((c.shape[0] + 2, c.shape[1] + 2, c.shape[2] + 2))
+    for a in range(c.shape[0]):
+        for b in range(c.shape[1]):
+            for g in range(c.shape[2]):
+                if c[a, b, g] != 0.0:
+                    out[a:a + 3, b:b + 3, g:g + 3] += c[a, b, g] * np.einsum("a,b,c->abc", bub, bub, bub)
+    return out
+
+
+def _poly3_laplacian(c):
+    out = np.zeros(c.shape)
+    for ax in range(3):
+        dd = P.polyder(c, 2, axis=ax)
+        sl = tuple(slice(0, s) for s in dd.shape)
+        out[sl] += dd
+    return out
+
+
+def manufactured_cube(pc: np.ndarray, n: int):
+    """(F, X_exact) for u = (1-x^2)(1-y^2)(1-z^2) p with p given by pc[a, b, g]."""
+    u = _poly3_bubble(pc)
+    f = _poly3_laplacian(u)
+    N = n + sum(u.shape) + 2
+    F = project_3d(lambda X, Y, Z: _poly3_eval(f, X, Y, Z), n, N)
+    Xe = project_3d(lambda X, Y, Z: _poly3_eval(pc, X, Y, Z), n, N)
+    return F, Xe

@@ -467,6 +467,219 @@ int orc_poisson_square_partial(long n, double tol, int jmax, const double *F, do
     return J;
 }
 
+
+/* ------------------------------------------------------------------------- */
+/* Section 5: the cube.  (D_xx + D_yy + D_zz) vec(X) = vec(F), eq. (5.2).      */
+/* In the symmetrised variables of (3.9) applied on every mode,                 */
+/*     (T_01 + T_02 + T_12) Y = G,   G = -F / sqrt(E_i E_j E_k),                */
+/*     X = Y / sqrt(E_i E_j E_k),                                               */
+/* where T_ab applies A~ on modes a and b of the n x n x n tensor (row-major,   */
+/* mode 0 = i, mode 1 = j, mode 2 = k).  The sign of G comes from the three     */
+/* factors D^{-1} = -E^{-1} (reading R11).  Nested ADI of Sec. 5 (readings      */
+/* R1, R12): outer split (5.3)-(5.4) H = T_01 + T_02 | V = T_12; middle split   */
+/* (5.5)-(5.6) of H + s into (T_01 + s/2) | (T_02 + s/2); inner slice Stein     */
+/* equations (5.7)-(5.9) (A~ Z A~ + c Z = R on two modes) by ADI on             */
+/* (c A~^{-1}) Z - Z (-A~) = A~^{-1} R.                                        */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    long n;
+    const real *d, *e; /* A~ bands (stride 2), e zero-padded to n */
+} cube_t;
+
+static long mode_stride(long n, int mode) { return mode == 0 ? n * n : (mode == 1 ? n : 1); }
+
+/* Y = (alpha A~ + beta I) X along `mode` (every line of the tensor in that mode). */
+static void t_apply(const cube_t *C, int mode, real alpha, real beta, const real *X, real *Y)
+{
+    long n = C->n, st = mode_stride(n, mode);
+    long nn = n * n;
+#pragma omp parallel for schedule(static)
+    for (long line = 0; line < nn; ++line) {
+        /* the two other indices of this line */
+        long o;
+        if (mode == 0) o = line;                          /* (j, k) = line */
+        else if (mode == 1) o = (line / n) * n * n + (line % n); /* (i, k) */
+        else o = line * n;                                /* (i, j) */
+        for (long t = 0; t < n; ++t) {
+            real v = (alpha * C->d[t] + beta) * X[o + t * st];
+            if (t >= 2) v += alpha * C->e[t - 2] * X[o + (t - 2) * st];
+            if (t + 2 < n) v += alpha * C->e[t] * X[o + (t + 2) * st];
+            Y[o + t * st] = v;
+        }
+    }
+}
+
+/* X = (alpha A~ + beta I)^{-1} R along `mode` (Thomas on the even and odd index
+ * sets of every line, App. B).  X may alias R. */
+static void t_solve(const cube_t *C, int mode, real alpha, real beta, const real *R, real *X)
+{
+    long n = C->n, st = mode_stride(n, mode);
+    long nn = n * n;
+    real *cp = malloc(sizeof(real) * (size_t)n), *den = malloc(sizeof(real) * (size_t)n);
+    for (long t = 0; t < n; ++t) {
+        real diag = alpha * C->d[t] + beta;
+        den[t] = (t >= 2) ? diag - alpha * C->e[t - 2] * cp[t - 2] : diag;
+        cp[t] = (t + 2 < n) ? alpha * C->e[t] / den[t] : 0;
+    }
+#pragma omp parallel for schedule(static)
+    for (long line = 0; line < nn; ++line) {
+        long o;
+        if (mode == 0) o = line;
+        else if (mode == 1) o = (line / n) * n * n + (line % n);
+        else o = line * n;
+        for (long t = 0; t < n; ++t) {
+            real v = R[o + t * st];
+            if (t >= 2) v -= alpha * C->e[t - 2] * X[o + (t - 2) * st];
+            X[o + t * st] = v / den[t];
+        }
+        for (long t = n - 1; t >= 0; --t)
+            if (t + 2 < n) X[o + t * st] -= cp[t] * X[o + (t + 2) * st];
+    }
+    free(cp);
+    free(den);
+}
+
+static void t_axpby(long N, real a, const real *X, real b, const real *Y, real *Z)
+{
+#pragma omp parallel for schedule(static)
+    for (long t = 0; t < N; ++t) Z[t] = a * X[t] + b * Y[t];
+}
+
+/* Z = (T_ab + c)^{-1} R, c > 0, i.e. the slice Stein equations A~_a Z A~_b + c Z = R
+ * of (5.7).  As in (5.8)-(5.9), a Sylvester equation for the slice:
+ * A~_a Z - Z (-c A~_b^{-1}) = R A~_b^{-1}, sigma(A~) in [-1, -eps] and
+ * sigma(-c A~^{-1}) in [c, c/eps]; Algorithm 2 in the sign-consistent form (R1),
+ * the first half-step multiplied through by A~_b on the right:
+ *   Z_h = [ R - (A~_a - p) Z A~_b ] (c + p A~_b)^{-1}
+ *   (A~_a - q) Z+ = (R - c Z_h) A~_b^{-1} - q Z_h                                */
+static int stein_solve(const cube_t *C, int ma, int mb, real c, real eps, double tol, const real *R, real *Z,
+                       real *W1, real *W2)
+{
+    long N = C->n * C->n * C->n;
+    double a = -1.0, b = -(double)eps, cc = (double)c, d = (double)(c / eps);
+    int J = orc_adi_iterations(a, b, cc, d, tol);
+    double *p = malloc(sizeof(double) * (size_t)J), *q = malloc(sizeof(double) * (size_t)J);
+    orc_adi_shifts(a, b, cc, d, tol, J, p, q);
+    memset(Z, 0, sizeof(real) * (size_t)N);
+    for (int l = 0; l < J; ++l) {
+        real pl = p[l], ql = q[l];
+        t_apply(C, mb, 1, 0, Z, W1);              /* Z A~_b */
+        t_apply(C, ma, 1, -pl, W1, W2);           /* (A~_a - p) ( . ) */
+        t_axpby(N, 1, R, -1, W2, W1);             /* R - ( . ) */
+        t_solve(C, mb, pl, c, W1, W2);            /* ( . ) (c + p A~_b)^{-1}: Z_h in W2 */
+        t_axpby(N, 1, R, -c, W2, W1);             /* R - c Z_h */
+        t_solve(C, mb, 1, 0, W1, W1);             /* ( . ) A~_b^{-1} */
+        t_axpby(N, 1, W1, -ql, W2, W1);           /* ... - q Z_h */
+        t_solve(C, ma, 1, -ql, W1, Z);            /* (A~_a - q)^{-1} */
+    }
+    free(p);
+    free(q);
+    return J;
+}
+
+/* Y = (T_01 + T_02 + s)^{-1} R, s > 0 (middle ADI, (5.5)-(5.6)): A' = T_01 + s/2,
+ * B' = T_02 + s/2 with spectra in [eps^2 + s/2, 1 + s/2]; shifts a_m there:
+ *   (B' + a) W_h = R - (A' - a) W,     (A' + a) W+ = R - (B' - a) W_h           */
+static long h_solve(const cube_t *C, real s, real eps, double tol_mid, double tol_in, const real *R, real *Y,
+                    real *Wh, real *T1, real *T2, real *S1, real *S2)
+{
+    long N = C->n * C->n * C->n;
+    double lo = (double)(eps * eps + s / 2), hi = (double)(1 + s / 2);
+    int J = orc_adi_iterations(-hi, -lo, lo, hi, tol_mid);
+    double *p = malloc(sizeof(double) * (size_t)J), *q = malloc(sizeof(double) * (size_t)J);
+    orc_adi_shifts(-hi, -lo, lo, hi, tol_mid, J, p, q);
+    long inner = 0;
+    memset(Y, 0, sizeof(real) * (size_t)N);
+    for (int m = 0; m < J; ++m) {
+        real am = q[m]; /* in [lo, hi] */
+        /* T1 = R - (T_01 + s/2 - a) Y */
+        t_apply(C, 0, 1, 0, Y, T1);
+        t_apply(C, 1, 1, 0, T1, T2);
+        t_axpby(N, 1, R, -1, T2, T1);
+        t_axpby(N, 1, T1, -(s / 2 - am), Y, T1);
+        inner += stein_solve(C, 0, 2, s / 2 + am, eps, tol_in, T1, Wh, S1, S2);
+        /* T1 = R - (T_02 + s/2 - a) Wh */
+        t_apply(C, 0, 1, 0, Wh, T1);
+        t_apply(C, 2, 1, 0, T1, T2);
+        t_axpby(N, 1, R, -1, T2, T1);
+        t_axpby(N, 1, T1, -(s / 2 - am), Wh, T1);
+        inner += stein_solve(C, 0, 1, s / 2 + am, eps, tol_in, T1, Y, S1, S2);
+    }
+    free(p);
+    free(q);
+    return inner;
+}
+
+/* Outer ADI (5.3)-(5.4) on H Y + V Y = G with H = T_01 + T_02 (sigma in [2 eps^2, 2])
+ * and V = T_12 (sigma in [eps^2, 1]), as A Y - Y B with A = H, B = -V:
+ *   (V + p) Y_h = G - (H - p) Y,     (H - q) Y+ = G - (V + q) Y_h,
+ * p in [2 eps^2, 2], q in [-1, -eps^2] (Appendix A with the roles of the two
+ * intervals exchanged to keep a < b < c < d). */
+static long cube_adi(const cube_t *C, real eps, double tol, double tol_mid, double tol_in, const real *G, real *Y,
+                     int *Jout)
+{
+    long N = C->n * C->n * C->n;
+    size_t bytes = sizeof(real) * (size_t)N;
+    real *Yh = malloc(bytes), *T1 = malloc(bytes), *T2 = malloc(bytes), *Wh = malloc(bytes);
+    real *H1 = malloc(bytes), *H2 = malloc(bytes), *S1 = malloc(bytes), *S2 = malloc(bytes);
+    double e2 = (double)(eps * eps);
+    int J = orc_adi_iterations(-1.0, -e2, 2 * e2, 2.0, tol);
+    double *pp = malloc(sizeof(double) * (size_t)J), *qq = malloc(sizeof(double) * (size_t)J);
+    orc_adi_shifts(-1.0, -e2, 2 * e2, 2.0, tol, J, pp, qq);
+    long inner = 0;
+    memset(Y, 0, bytes);
+    for (int j = 0; j < J; ++j) {
+        real p = qq[j], q = pp[j]; /* p in sigma(H)'s interval, q in sigma(-V)'s */
+        /* T1 = G - (H - p) Y */
+        t_apply(C, 0, 1, 0, Y, T1);
+        t_apply(C, 1, 1, 0, T1, T2);   /* T_01 Y */
+        t_apply(C, 2, 1, 0, T1, H1);   /* T_02 Y */
+        t_axpby(N, 1, T2, 1, H1, T2);
+        t_axpby(N, 1, G, -1, T2, T1);
+        t_axpby(N, 1, T1, p, Y, T1);
+        inner += stein_solve(C, 1, 2, p, eps, tol_in, T1, Yh, S1, S2);
+        /* T1 = G - (V + q) Y_h */
+        t_apply(C, 1, 1, 0, Yh, T1);
+        t_apply(C, 2, 1, 0, T1, T2);   /* T_12 Y_h */
+        t_axpby(N, 1, G, -1, T2, T1);
+        t_axpby(N, 1, T1, -q, Yh, T1);
+        inner += h_solve(C, -q, eps, tol_mid, tol_in, T1, Y, Wh, T2, H1, S1, S2);
+    }
+    free(pp); free(qq);
+    free(Yh); free(T1); free(T2); free(Wh); free(H1); free(H2); free(S1); free(S2);
+    if (Jout) *Jout = J;
+    return inner;
+}
+
+/* Cube end to end: F (n^3, row-major, X_ijk pairs C~_i C~_j C~_k) -> X.
+ * Returns the number of inner (slice-Stein) ADI iterations over full tensors. */
+long orc_poisson_cube(long n, double tol, double tol_mid, double tol_in, const double *F, double *X, int *Jout)
+{
+    long N = n * n * n;
+    real *d = malloc(sizeof(real) * (size_t)n), *e = calloc((size_t)n, sizeof(real));
+    square_bands(n, d, e);
+    cube_t C = {n, d, e};
+    real *G = malloc(sizeof(real) * (size_t)N), *Y = malloc(sizeof(real) * (size_t)N);
+    for (long i = 0; i < n; ++i)
+        for (long j = 0; j < n; ++j)
+            for (long k = 0; k < n; ++k) {
+                long t = (i * n + j) * n + k;
+                real s = Ds_diag(i) * Ds_diag(j) * Ds_diag(k); /* |D|^{-1/2} on every mode */
+                G[t] = -(real)F[t] * s;
+            }
+    real eps = 1 / ((real)30 * (real)n * (real)n * (real)n * (real)n);
+    long inner = cube_adi(&C, eps, tol, tol_mid, tol_in, G, Y, Jout);
+    for (long i = 0; i < n; ++i)
+        for (long j = 0; j < n; ++j)
+            for (long k = 0; k < n; ++k) {
+                long t = (i * n + j) * n + k;
+                X[t] = (double)(Y[t] * Ds_diag(i) * Ds_diag(j) * Ds_diag(k));
+            }
+    free(d); free(e); free(G); free(Y);
+    return inner;
+}
+
 /* Threads OpenMP will use (reported beside the CPU-baseline timings). */
 int orc_num_threads(void)
 {
