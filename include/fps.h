@@ -116,9 +116,12 @@ int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X);
 
 /*
  * fps_poisson_cube_solve -- X = solution of (5.2) on [-1,1]^3 by the nested ADI of
- * Sec. 5 (outer split (D_xx + D_yy) | D_zz, middle split D_xx | D_yy, inner
- * Stein equations per slice).  Errors: INVALID_ARG (plan not dim 3), UNSUPPORTED
- * when this build has no cube path, CUDA.
+ * Sec. 5: outer split (T_01 + T_02) | T_12 of the symmetrised operator, middle
+ * split of T_01 + T_02 + s into two halves, inner Stein equations
+ * A~ Z A~ + c Z = R on every slice; outer tolerance = the plan's tol, middle and
+ * inner 1e-15.  Plans: dim = 3, FPS_FP64, n <= 320.  X[(i*n + j)*n + k] pairs
+ * C~_i(x) C~_j(y) C~_k(z).  Errors: INVALID_ARG (plan not dim 3, NULL/overlapping
+ * buffers), UNSUPPORTED (FP32_REFINE or n > 320 at plan creation), CUDA.
  */
 int fps_poisson_cube_solve(fps_plan *plan, const double *F, double *X);
 

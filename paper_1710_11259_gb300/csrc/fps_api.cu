@@ -11,6 +11,7 @@
 #include "host_math.h"
 #include "kernels.cuh"
 #include "refine_engine.h"
+#include "cube.h"
 
 namespace {
 
@@ -79,6 +80,8 @@ struct fps_plan {
 
     // FPS_FP32_REFINE (single problem or batch): the refinement engine
     fps::RefineEngine *eng = nullptr;
+    // dim = 3: the nested cube ADI
+    fps::CubeEngine *cube = nullptr;
     std::vector<int64_t> batch_ns;   // sizes of a batched plan (empty otherwise)
     int64_t total_elems = 0;         // doubles in F (and X) for all right-hand sides / problems
     double *stage_in = nullptr, *stage_out = nullptr;  // lazily allocated for host pointers
@@ -112,6 +115,10 @@ void release(fps_plan *p)
     if (p->eng) {
         p->eng->release();
         delete p->eng;
+    }
+    if (p->cube) {
+        p->cube->release();
+        delete p->cube;
     }
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
@@ -260,7 +267,34 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     if (nrhs < 1) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: nrhs must be >= 1");
     if (precision != FPS_FP64 && precision != FPS_FP32_REFINE)
         return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: unknown precision");
-    if (dim == 3) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the cube path is not built yet");
+    if (dim == 3) {
+        if (precision != FPS_FP64)
+            return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the cube runs in FPS_FP64 only");
+        if (n > 320) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the cube supports n <= 320");
+        fps_plan *p = new fps_plan();
+        p->n = n;
+        p->dim = 3;
+        p->tol = tol;
+        p->precision = precision;
+        p->nrhs = nrhs;
+        p->stream = (cudaStream_t)stream;
+        p->total_elems = n * n * n * nrhs;
+        if (cudaGetDevice(&p->device) != cudaSuccess) {
+            delete p;
+            return fail(FPS_ERR_CUDA, "fps_plan_create: no CUDA device");
+        }
+        p->cube = new fps::CubeEngine();
+        std::string err;
+        const int st = p->cube->create(n, tol, 1e-15, 1e-15, err);
+        if (st != FPS_OK) {
+            release(p);
+            return fail(st, "fps_plan_create: " + err);
+        }
+        p->J = p->cube->J_outer;
+        p->bytes = p->cube->bytes;
+        *out = p;
+        return FPS_OK;
+    }
 
     fps_plan *p = new fps_plan();
     p->n = n;
@@ -391,10 +425,42 @@ int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X)
 
 int fps_poisson_cube_solve(fps_plan *plan, const double *F, double *X)
 {
-    (void)F; (void)X;
     if (!plan) return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: plan is NULL");
-    if (plan->dim != 3) return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: plan is not three-dimensional");
-    return fail(FPS_ERR_UNSUPPORTED, "fps_poisson_cube_solve: not built yet");
+    if (plan->dim != 3 || !plan->cube)
+        return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: plan is not three-dimensional");
+    if (!F || !X) return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: NULL F or X");
+    const int64_t n3 = plan->n * plan->n * plan->n;
+    const size_t bytes = sizeof(double) * (size_t)plan->total_elems;
+    const char *f0 = (const char *)F, *x0 = (const char *)X;
+    if (f0 < x0 + bytes && x0 < f0 + bytes) return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: F and X overlap");
+    DeviceGuard g(plan->device);
+    const bool fdev = is_device_pointer(F), xdev = is_device_pointer(X);
+    if ((!fdev || !xdev) && !plan->stage_in) {
+        FPS_CK(cudaMalloc((void **)&plan->stage_in, sizeof(double) * n3));
+        FPS_CK(cudaMalloc((void **)&plan->stage_out, sizeof(double) * n3));
+    }
+    plan->launches_last = 0;
+    for (int r = 0; r < plan->nrhs; ++r) {
+        const double *Fr = F + (int64_t)r * n3;
+        double *Xr = X + (int64_t)r * n3;
+        const double *Fd = Fr;
+        double *Xd = xdev ? Xr : plan->stage_out;
+        if (!fdev) {
+            FPS_CK(cudaMemcpyAsync(plan->stage_in, Fr, sizeof(double) * n3, cudaMemcpyHostToDevice, plan->stream));
+            Fd = plan->stage_in;
+        }
+        std::string err;
+        const int st = plan->cube->solve_cube(Fd, Xd, plan->stream, err);
+        if (st != FPS_OK) return fail(st, "fps_poisson_cube_solve: " + err);
+        plan->launches_last += plan->cube->launches_last;
+        if (!xdev) {
+            FPS_CK(cudaMemcpyAsync(Xr, Xd, sizeof(double) * n3, cudaMemcpyDeviceToHost, plan->stream));
+            FPS_CK(cudaStreamSynchronize(plan->stream));
+        }
+    }
+    if (!fdev && xdev) FPS_CK(cudaStreamSynchronize(plan->stream));
+    FPS_CK(cudaGetLastError());
+    return FPS_OK;
 }
 
 int fps_poisson_adjoint(fps_plan *plan, const double *dLdX, double *dLdF)
