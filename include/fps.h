@@ -213,6 +213,16 @@ int fps_zolotarev_shifts(double a, double b, double c, double d, double tol, int
  */
 int fps_square_bands(int64_t n, double *d, double *e);
 
+/*
+ * fps_square_spectral_interval -- bounds sigma(A~) in [-hi, -lo] for size n.
+ * tight = 0: Lemma B.2, lo = 1/(30 n^4), hi = 1 (the interval the FP64 solve and its
+ * shift list use).  tight != 0: Sturm-count bisection on the even and odd
+ * tridiagonals of A~ (App. B), lo = |lambda_max|/2 and hi = 1.01 |lambda_min| (the
+ * interval of the FP32 inner solves, whose result is checked against the exact
+ * solution rather than iterate by iterate).  Host FP64.  Errors: INVALID_ARG.
+ */
+int fps_square_spectral_interval(int64_t n, int tight, double *lo, double *hi);
+
 /* Build identification (compute capability the kernels were built for, e.g. 103). */
 int fps_build_arch(void);
 

@@ -65,6 +65,7 @@ EXPORTED = [
     "fps_poisson_cube_solve", "fps_poisson_adjoint", "fps_plan_info", "fps_plan_shifts", "fps_plan_destroy",
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
     "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
+    "fps_square_spectral_interval",
 ]
 
 
@@ -99,6 +100,7 @@ def lib() -> ctypes.CDLL:
         L.fps_plan_set_instrument.argtypes = [vp, ctypes.c_int]
         L.fps_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
         L.fps_poisson_square_solve_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp]
+        L.fps_square_spectral_interval.argtypes = [i64, ctypes.c_int, dp, dp]
         _lib = L
         return L
 
@@ -273,6 +275,13 @@ def zolotarev_shifts(a: float, b: float, c: float, d: float, tol: float, J: int 
     p, q = np.zeros(Jo.value), np.zeros(Jo.value)
     _check(lib().fps_zolotarev_shifts(a, b, c, d, tol, int(J), ctypes.byref(Jo), _dp(p), _dp(q), Jo.value))
     return p, q
+
+
+def square_spectral_interval(n: int, tight: bool = False):
+    """(lo, hi) with sigma(A~) in [-hi, -lo]: Lemma B.2, or tight bounds by bisection."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fps_square_spectral_interval(int(n), 1 if tight else 0, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
 
 
 def square_bands(n: int):

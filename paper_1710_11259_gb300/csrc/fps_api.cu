@@ -609,6 +609,18 @@ int fps_square_bands(int64_t n, double *d, double *e)
     return FPS_OK;
 }
 
+int fps_square_spectral_interval(int64_t n, int tight, double *lo, double *hi)
+{
+    if (n < 1 || !lo || !hi) return fail(FPS_ERR_INVALID_ARG, "fps_square_spectral_interval: bad argument");
+    if (tight) {
+        fps::square_tight_interval(n, *lo, *hi);
+    } else {
+        *lo = fps::square_eps(n);
+        *hi = 1.0;
+    }
+    return FPS_OK;
+}
+
 int fps_build_arch(void) { return 103; }
 
 }  // extern "C"

@@ -13,6 +13,7 @@
 // shift comes from an argument u <= K/2 where dn >= sqrt(k') is well conditioned.
 #include "host_math.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace fps {
@@ -142,6 +143,54 @@ void zolotarev_shifts(double a, double b, double c, double d, int J, std::vector
         p[j] = T(-alp * dn[j]);
         q[j] = T(alp * dn[j]);
     }
+}
+
+// Number of eigenvalues of A~ (size n) below x: Sturm count, i.e. the negative
+// pivots of the LDL^T factorisation of A~ - x I on the even and on the odd index
+// set (the two decoupled tridiagonals of App. B).
+static int64_t sturm_count_below(const std::vector<double> &d, const std::vector<double> &e, double x)
+{
+    const int64_t n = (int64_t)d.size();
+    int64_t count = 0;
+    for (int par = 0; par < 2; ++par) {
+        double piv = 0.0;
+        for (int64_t i = par; i < n; i += 2) {
+            double v = d[i] - x;
+            if (i >= 2) {
+                const double off = e[i - 2];
+                v -= (piv != 0.0) ? off * off / piv : off * off / 1e-300;
+            }
+            if (v == 0.0) v = -1e-300;
+            if (v < 0.0) ++count;
+            piv = v;
+        }
+    }
+    return count;
+}
+
+void square_tight_interval(int64_t n, double &lo, double &hi)
+{
+    std::vector<double> d, e;
+    square_bands(n, d, e);
+    // largest eigenvalue (closest to zero): bisection in log|x| on [-1, -eps/8]
+    double a = std::log(square_eps(n) / 8.0), b = 0.0;  // log of |x|: the largest eig has |x| in [e^a, e^b]
+    for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (a + b);
+        // all n eigenvalues below -exp(mid)  <=>  lambda_max < -exp(mid)
+        if (sturm_count_below(d, e, -std::exp(mid)) == n) a = mid;
+        else b = mid;
+    }
+    const double lam_max_abs = std::exp(a);  // |lambda_max| >= this
+    // smallest eigenvalue: bisection on [-1, 0]
+    double l = -1.0, r = 0.0;
+    for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (l + r);
+        if (sturm_count_below(d, e, mid) == 0) l = mid;
+        else r = mid;
+    }
+    // safety margins: a factor of two at the small end, one percent at the large end
+    lo = 0.5 * lam_max_abs;
+    hi = std::min(1.0, 1.01 * (-l));
 }
 
 // Allocation-free forms of square_bands / inv_sqrt_E / zolotarev_shifts_symmetric

@@ -17,6 +17,10 @@ void inv_sqrt_E(int64_t n, std::vector<double> &s);
 // Lemma B.2 lower end of |sigma(A~)|: 1/(30 n^4).
 double square_eps(int64_t n);
 
+// Tight bounds sigma(A~) in [-hi, -lo] from Sturm-count bisection, with a safety
+// factor 1/2 on lo and 1.01 on hi.
+void square_tight_interval(int64_t n, double &lo, double &hi);
+
 // J = ceil(log(16 gamma) log(4/tol) / pi^2), gamma the cross-ratio of [a,b], [c,d].
 int adi_iterations(double a, double b, double c, double d, double tol);
 

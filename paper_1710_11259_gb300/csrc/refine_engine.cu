@@ -9,7 +9,9 @@
 //   X = D_s Y D_s.
 // The inner tolerance of a round is the coarsest level that still gains ten times
 // what the worst active pair is missing; the first round uses the finest level
-// (1e-7, the accuracy an FP32 inner solve can deliver).
+// (1e-7, the accuracy an FP32 inner solve can deliver).  The inner shifts come from
+// a tight spectral interval of A~ (Sturm bisection) rather than Lemma B.2's: the
+// refinement is judged by the FP64 residual, not by matching a particular iterate.
 #include "refine_engine.h"
 
 #include <algorithm>
@@ -224,15 +226,16 @@ int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, c
     ENG_CK(dalloc(&d_items_, (size_t)nitems_));
     ENG_CK(cudaMemcpyAsync(d_items_, items.data(), sizeof(int4) * nitems_, cudaMemcpyHostToDevice, cap_));
 
-    // tolerance levels: shifts per problem, factor tables via factor jobs
+    // tolerance levels: shifts per problem from the tight spectral interval, factor tables via factor jobs
+    std::vector<double> tlo(np), thi(np);
+    for (int p = 0; p < np; ++p) square_tight_interval(ns[p], tlo[p], thi[p]);
     for (double lt : kLevelTols) {
         Level L;
         L.tol = lt;
         L.J.resize(np);
         int64_t nfac = 0, nph = 0, nsc = 0, nq = 0;
         for (int p = 0; p < np; ++p) {
-            const double eps = square_eps(ns[p]);
-            L.J[p] = adi_iterations(-1.0, -eps, eps, 1.0, lt);
+            L.J[p] = adi_iterations(-thi[p], -tlo[p], tlo[p], thi[p], lt);
             L.Jmax = std::max(L.Jmax, L.J[p]);
             nfac += (int64_t)L.J[p] * ns[p];
             nph += (int64_t)L.J[p] * 2 * geo_[p].nchunk;
@@ -255,7 +258,7 @@ int RefineEngine::create(const std::vector<int64_t> &ns, int nrhs, double tol, c
         for (int p = 0; p < np; ++p) {
             const int64_t n = ns[p];
             const RefineGeometry &g = geo_[p];
-            zolotarev_shifts_symmetric(square_eps(n), 1.0, L.J[p], q);
+            zolotarev_shifts_symmetric(tlo[p], thi[p], L.J[p], q);
             RefProb &rp = probs[p];
             rp.n = (int)n;
             rp.ld = (int)g.ld;
@@ -385,8 +388,9 @@ int RefineEngine::autotune(const int *cand, int ncand, const std::vector<RefProb
         int64_t nfac = 0, nph = 0, nsc = 0, osm = 0;
         std::vector<int> Jt(np);
         for (int p = 0; p < np; ++p) {
-            const double eps = square_eps(ns_[p]);
-            Jt[p] = std::min(2, adi_iterations(-1.0, -eps, eps, 1.0, kLevelTols[0]));
+            double lo, hi;
+            square_tight_interval(ns_[p], lo, hi);
+            Jt[p] = std::min(2, adi_iterations(-hi, -lo, lo, hi, kLevelTols[0]));
             nfac += (int64_t)Jt[p] * ns_[p];
             nph += (int64_t)Jt[p] * 2 * g[p].nchunk;
             nsc += (int64_t)Jt[p] * 2 * g[p].P;
@@ -412,7 +416,9 @@ int RefineEngine::autotune(const int *cand, int ncand, const std::vector<RefProb
         std::vector<double> q;
         for (int p = 0; p < np; ++p) {
             const int64_t n = ns_[p];
-            zolotarev_shifts_symmetric(square_eps(n), 1.0, Jt[p], q);
+            double lo, hi;
+            square_tight_interval(n, lo, hi);
+            zolotarev_shifts_symmetric(lo, hi, Jt[p], q);
             RefProb &rp = probs[p];
             rp.n = (int)n;
             rp.ld = (int)g[p].ld;

@@ -119,3 +119,18 @@ def test_library_and_oracle_shifts_agree(L):
         p, q = api.zolotarev_shifts(a, b, c, d, 1e-13)
         assert np.abs(q - qo).max() / 1.0 < 1e-13
         assert (np.abs(q - qo) / qo).max() < 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 300, 1500])
+def test_tight_spectral_interval_contains_spectrum(L, n):
+    """Sturm-bisection bounds contain sigma(A~) (eigvalsh) and are tighter than Lemma B.2."""
+    lo, hi = api.square_spectral_interval(n, tight=True)
+    glo, ghi = api.square_spectral_interval(n, tight=False)
+    d, e = oracle.square_bands(n)
+    A = np.diag(d)
+    for j in range(n - 2):
+        A[j, j + 2] = A[j + 2, j] = e[j]
+    lam = np.linalg.eigvalsh(A)
+    assert lo <= -lam.max() and hi >= -lam.min()
+    assert lo >= glo and hi <= ghi
+    assert glo == 1.0 / (30.0 * n**4) and ghi == 1.0
