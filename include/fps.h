@@ -64,15 +64,19 @@ typedef struct {
     int precision;          /* fps_precision */
     int nrhs;               /* right-hand sides per problem */
     int64_t batch;          /* problems in the plan (1 unless batched) */
-    int J;                  /* ADI iterations of the FP64 solve, eq. (2.9) */
-    int J_inner;            /* ADI iterations per refinement round (FP32_REFINE) */
+    int J;                  /* ADI iterations of the FP64 solve, eq. (2.9) (cube: outer level) */
+    int J_inner;            /* ADI iterations per refinement round (FP32_REFINE; cube: outer
+                               level of a round) */
     int refine_rounds;      /* rounds used by the last FP32_REFINE solve */
-    double last_residual;   /* max |R~| / max |F~| after the last FP32_REFINE solve */
+    double last_residual;   /* max |R~| / max |F~| (cube: max |R| / max |G|) after the last
+                               FP32_REFINE solve */
     double tol;             /* requested tolerance */
     int64_t device_bytes;   /* device memory owned by the plan */
     int64_t kernel_launches; /* kernels of this library launched by the last solve */
     int pass_ctas;          /* FP32_REFINE: CTAs per pass aimed at on the largest problem
                                (picked by the autotuner unless FPS_AUTOTUNE=0) */
+    int64_t inner_iterations; /* cube: inner (slice Stein) ADI iterations over full
+                                 tensors in the last solve, all levels and rounds */
 } fps_plan_info_t;
 
 /*
@@ -118,10 +122,16 @@ int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X);
  * fps_poisson_cube_solve -- X = solution of (5.2) on [-1,1]^3 by the nested ADI of
  * Sec. 5: outer split (T_01 + T_02) | T_12 of the symmetrised operator, middle
  * split of T_01 + T_02 + s into two halves, inner Stein equations
- * A~ Z A~ + c Z = R on every slice; outer tolerance = the plan's tol, middle and
- * inner 1e-15.  Plans: dim = 3, FPS_FP64, n <= 320.  X[(i*n + j)*n + k] pairs
- * C~_i(x) C~_j(y) C~_k(z).  Errors: INVALID_ARG (plan not dim 3, NULL/overlapping
- * buffers), UNSUPPORTED (FP32_REFINE or n > 320 at plan creation), CUDA.
+ * A~ Z A~ + c Z = R on every slice.  FPS_FP64: outer tolerance = the plan's tol,
+ * middle and inner 1e-15, the paper's form of every level.  FPS_FP32_REFINE: the
+ * nested ADI in FP32, every level in residual-propagating form, with level
+ * tolerances (1e-3, 1e-6, 1e-7), inside an FP64 defect correction on the residual
+ * R = G - (T_01 + T_02 + T_12) Y of the symmetrised equation (G = -F/sqrt(E_i E_j E_k))
+ * until max |R| / max |G| <= tol (at most 12 rounds).  Plans: dim = 3, n <= 320.
+ * X[(i*n + j)*n + k] pairs C~_i(x) C~_j(y) C~_k(z).  Host or device F and X.
+ * Errors: INVALID_ARG (plan not dim 3, NULL/overlapping buffers), UNSUPPORTED
+ * (n > 320 at plan creation), NONFINITE (FP32_REFINE: F holds NaN/Inf),
+ * NOT_CONVERGED (FP32_REFINE missed tol; X holds the last iterate), CUDA.
  */
 int fps_poisson_cube_solve(fps_plan *plan, const double *F, double *X);
 

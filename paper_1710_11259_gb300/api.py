@@ -54,6 +54,7 @@ class PlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
         ("pass_ctas", ctypes.c_int),
+        ("inner_iterations", ctypes.c_int64),
     ]
 
 

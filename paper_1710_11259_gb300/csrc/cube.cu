@@ -10,13 +10,24 @@
 //          (A~_a - q) Z+ = (R - c Z_h) A~_b^{-1} - q Z_h
 // Every operation is a banded product or a banded (even/odd decoupled, App. B)
 // solve along one mode of the whole tensor: all slices of a level are solved at
-// once.  Modes 0 and 1 are solved with one thread per (line, parity), coalesced
-// across the contiguous index; mode 2 (contiguous lines) goes through a
-// shared-memory tile of 32 lines.
+// once.  The solves run one thread per (line, parity) over 32 lines per CTA with
+// coalesced global traffic.  The same kernels run in FP64 and in FP32.
+//
+// FP32 + refinement: the nested ADI (every level in residual-propagating form, see
+// run_residual, hsolve_res, stein_res) runs in FP32 at loose level tolerances on
+// the normalised residual rho = R / max|R|, R = G - (T_01 + T_02 + T_12) Y computed
+// in FP64 (a 27-point product), and Y += max|R| * delta accumulates in FP64, until
+// max|R| / max|G| meets the plan's tolerance.  The defect correction only needs
+// each round's correction to reduce the residual, so the loose inner levels make a
+// round several times cheaper than one solve at the paper's 1e-15 inner levels.
+//
+// Index arithmetic inside the kernels is 32-bit where it divides: plans cap n at
+// 320, so n^3 < 2^31.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -28,23 +39,32 @@ namespace fps {
 
 namespace {
 
-constexpr int kLines = 32;  // lines per CTA of the contiguous-mode solve
+constexpr int kLines = 32;  // lines per CTA of the solve kernels
+constexpr int kU = 8;       // rows of global loads in flight per thread in the solve kernels
 
-__device__ __forceinline__ int64_t mode_stride(int n, int mode)
-{
-    return mode == 0 ? (int64_t)n * n : (mode == 1 ? (int64_t)n : 1);
-}
+template <typename T>
+struct V2;
+template <>
+struct V2<double> {
+    using type = double2;
+    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+template <>
+struct V2<float> {
+    using type = float2;
+    static __device__ __forceinline__ float2 make(double a, double b) { return make_float2((float)a, (float)b); }
+};
 
-// Y = sop * ((alpha A~ + beta) X along `mode`) + sr * R   (R may be null)
-__global__ void cube_band_kernel(const double *__restrict__ X, const double *__restrict__ R, double *__restrict__ Y,
-                                 const double *__restrict__ d, const double *__restrict__ e, int n, int mode,
-                                 double alpha, double beta, double sop, double sr)
+// Y = sop * ((alpha A~ + beta) X along `mode`) + sr * R   (R may be null; Y may alias R)
+template <typename T>
+__global__ void cube_band_kernel(const T *__restrict__ X, const T *R, T *Y, const T *__restrict__ d,
+                                 const T *__restrict__ e, int n, int mode, T alpha, T beta, T sop, T sr)
 {
-    const int64_t N = (int64_t)n * n * n;
-    const int64_t st = mode_stride(n, mode);
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)((idx / st) % n);
-        double v = (alpha * d[t] + beta) * X[idx];
+    const int N = n * n * n;
+    const int st = (mode == 0) ? n * n : ((mode == 1) ? n : 1);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+        const int t = (mode == 0) ? idx / (n * n) : ((mode == 1) ? (idx / n) % n : idx % n);
+        T v = (alpha * d[t] + beta) * X[idx];
         if (t >= 2) v = fma(alpha * e[t - 2], X[idx - 2 * st], v);
         if (t + 2 < n) v = fma(alpha * e[t], X[idx + 2 * st], v);
         v *= sop;
@@ -53,18 +73,28 @@ __global__ void cube_band_kernel(const double *__restrict__ X, const double *__r
     }
 }
 
-// Z = a X + b Y
-__global__ void cube_axpby_kernel(const double *__restrict__ X, const double *__restrict__ Y, double *__restrict__ Z,
-                                  int64_t N, double a, double b)
+// Z = a X + b Y (element-wise; Z may alias X or Y)
+template <typename T>
+__global__ void cube_axpby_kernel(const T *X, const T *Y, T *Z, int N, T a, T b)
 {
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x)
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x)
         Z[idx] = fma(a, X[idx], b * Y[idx]);
 }
 
-// Thomas factors of (alpha A~ + beta I) for a list of (alpha, beta) pairs: one
-// thread per (set, parity); fac[set * n + t] = {1/den_t, alpha e_t / den_t}.
+// V = a X + b Y + c W (element-wise; V may alias any input)
+template <typename T>
+__global__ void cube_axpy3_kernel(const T *X, const T *Y, const T *W, T *V, int N, T a, T b, T c)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x)
+        V[idx] = fma(a, X[idx], fma(b, Y[idx], c * W[idx]));
+}
+
+// Thomas factors of (alpha A~ + beta I) for a list of (alpha, beta) pairs, computed
+// in FP64 and stored in T: one thread per (set, parity); fac[set * n + t] =
+// {1/den_t, alpha e_t / den_t}.
+template <typename T>
 __global__ void cube_factor_kernel(const double *__restrict__ d, const double *__restrict__ e, int n,
-                                   const double2 *__restrict__ ab, int nsets, double2 *__restrict__ fac)
+                                   const double2 *__restrict__ ab, int nsets, typename V2<T>::type *__restrict__ fac)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= 2 * nsets) return;
@@ -76,294 +106,743 @@ __global__ void cube_factor_kernel(const double *__restrict__ d, const double *_
         if (t >= 2) den -= alpha * e[t - 2] * u_prev;
         const double ip = 1.0 / den;
         const double u = alpha * e[t] * ip;
-        fac[(int64_t)set * n + t] = make_double2(ip, u);
+        fac[(int64_t)set * n + t] = V2<T>::make(ip, u);
         u_prev = u;
     }
 }
 
-// X = (alpha A~ + beta)^{-1} (s1 R1 + s2 R2) along mode 0 or 1; X may alias R1/R2
-// only element-wise (each thread reads an element before it writes it).
-__global__ void cube_solve_strided_kernel(const double2 *__restrict__ fac, const double *R1, double s1,
-                                          const double *R2, double s2, double *X, int n, int mode)
+// X = oscale (alpha A~ + beta)^{-1} (s1 R1 + s2 R2) + oacc X along mode 0 or 1
+// (oacc = 0: X is not read).  X may alias R1/R2 when oacc = 0: each element is
+// read and written by one thread, the read first.
+// CTA = 2 warps over kLines lines adjacent in mode 2: warp = parity, lane = line,
+// so every load and store of a step is one coalesced row of the tensor.  The
+// forward sweep reads kU rows ahead of the recurrence and keeps its z values in
+// shared memory for the backward sweep, which writes X directly.
+// Grid: one CTA per (index of the other strided mode, block of kLines in mode 2).
+template <typename T>
+__global__ void __launch_bounds__(64) cube_solve_strided_kernel(const typename V2<T>::type *__restrict__ fac,
+                                                                const T *R1, T s1, const T *R2, T s2, T *X, int n,
+                                                                int mode, T oscale, T oacc)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int half = (n + 1) / 2;
+    const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
+    T *zs = reinterpret_cast<T *>(smem_raw) + par * half * kLines;  // [half][kLines] of this parity
+    const int nkb = (n + kLines - 1) / kLines;
+    const int other = blockIdx.x / nkb, k0 = (blockIdx.x % nkb) * kLines;
+    const bool act = k0 + lane < n;
     const int64_t nn = (int64_t)n * n;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= 2 * nn) return;
-    const int par = (int)(tid / nn);
-    const int64_t line = tid - par * nn;
-    const int64_t st = (mode == 0) ? nn : (int64_t)n;
-    const int64_t o = (mode == 0) ? line : (line / n) * nn + (line % n);
-    double z = 0.0, u_prev = 0.0;
-    for (int t = par; t < n; t += 2) {
-        const int64_t at = o + (int64_t)t * st;
-        double r = s1 * R1[at];
-        if (R2) r = fma(s2, R2[at], r);
-        z = fma(-u_prev, z, r);
-        X[at] = z;
-        u_prev = fac[t].y;
+    const int64_t st = (mode == 0) ? nn : (int64_t)n;                 // stride of the solved mode
+    const int64_t st2 = 2 * st;
+    const int64_t o = ((mode == 0) ? (int64_t)other * n : (int64_t)other * nn) + k0 + lane + par * st;  // t = par
+    const int m = (n - par + 1) / 2;  // unknowns of this parity
+    T z = 0, u_prev = 0;
+    for (int i0 = 0; i0 < m; i0 += kU) {
+        T r[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            r[u] = 0;
+            if (act && i0 + u < m) {
+                const int64_t at = o + (int64_t)(i0 + u) * st2;
+                T v = s1 * R1[at];
+                if (R2) v = fma(s2, R2[at], v);
+                r[u] = v;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u;
+            if (i < m) {
+                z = fma(-u_prev, z, r[u]);
+                zs[i * kLines + lane] = z;
+                u_prev = fac[par + 2 * i].y;
+            }
+        }
     }
-    double x = 0.0;
-    const int tlast = par + 2 * ((n - 1 - par) / 2);
-    for (int t = tlast; t >= 0; t -= 2) {
-        const int64_t at = o + (int64_t)t * st;
-        const double2 f = fac[t];
-        x = fma(-f.y, x, f.x * X[at]);
-        X[at] = x;
+    __syncwarp();
+    T x = 0;
+    for (int i0 = m - 1; i0 >= 0; i0 -= kU) {
+        T xo[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            xo[u] = 0;
+            if (oacc != T(0) && act && i0 - u >= 0) xo[u] = X[o + (int64_t)(i0 - u) * st2];
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 - u;
+            if (i >= 0) {
+                const auto f = fac[par + 2 * i];
+                x = fma(-f.y, x, f.x * zs[i * kLines + lane]);
+                if (act) {
+                    const T v = oscale * x;
+                    X[o + (int64_t)i * st2] = (oacc != T(0)) ? fma(oacc, xo[u], v) : v;
+                }
+            }
+        }
     }
 }
 
-// Same along mode 2 (contiguous lines) through a shared-memory tile of kLines lines.
-__global__ void cube_solve_contig_kernel(const double2 *__restrict__ fac, const double *R1, double s1,
-                                         const double *R2, double s2, double *X, int n)
+// Shared-memory row pitch of the contiguous-mode tile: odd, so that the 32 lanes
+// of a warp (one line each, same t) hit distinct banks.
+__host__ __device__ __forceinline__ int contig_pitch(int n) { return (n % 2 == 0) ? n + 1 : n + 2; }
+
+// Same along mode 2 (contiguous lines): a CTA loads kLines consecutive lines into a
+// shared-memory tile (coalesced, kU rows in flight per thread), runs the sweeps of
+// each (line, parity) there (warp = parity, lane = line), and writes the tile back.
+template <typename T>
+__global__ void __launch_bounds__(64) cube_solve_contig_kernel(const typename V2<T>::type *__restrict__ fac,
+                                                               const T *R1, T s1, const T *R2, T s2, T *X, int n,
+                                                               T oscale, T oacc)
 {
-    extern __shared__ double tile[];  // kLines x (n + 1)
-    const int64_t nlines = (int64_t)n * n;
-    const int64_t L0 = (int64_t)blockIdx.x * kLines;
-    const int pitch = n + 1;
-    const int64_t base = L0 * n;
-    const int64_t count = ((nlines - L0 < kLines) ? (nlines - L0) : (int64_t)kLines) * n;
-    for (int64_t idx = threadIdx.x; idx < count; idx += blockDim.x) {
-        double r = s1 * R1[base + idx];
-        if (R2) r = fma(s2, R2[base + idx], r);
-        tile[(idx / n) * pitch + (idx % n)] = r;
-    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);  // kLines x pitch
+    const int pitch = contig_pitch(n);
+    const int nlines = n * n;
+    const int L0 = blockIdx.x * kLines;
+    const int nl = min(kLines, nlines - L0);
+    const int64_t base = (int64_t)L0 * n;
+    for (int li0 = 0; li0 < nl; li0 += kU)
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            T r[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                r[u] = 0;
+                if (li0 + u < nl) {
+                    const int64_t at = base + (int64_t)(li0 + u) * n + t;
+                    T v = s1 * R1[at];
+                    if (R2) v = fma(s2, R2[at], v);
+                    r[u] = v;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (li0 + u < nl) tile[(li0 + u) * pitch + t] = r[u];
+        }
     __syncthreads();
-    const int lane_line = threadIdx.x >> 1, par = threadIdx.x & 1;
-    if (lane_line < kLines && L0 + lane_line < nlines) {
-        double *row = tile + lane_line * pitch;
-        double z = 0.0, u_prev = 0.0;
+    const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
+    if (lane < nl) {
+        T *row = tile + lane * pitch;
+        T z = 0, u_prev = 0;
         for (int t = par; t < n; t += 2) {
             z = fma(-u_prev, z, row[t]);
             row[t] = z;
             u_prev = fac[t].y;
         }
-        double x = 0.0;
+        T x = 0;
         const int tlast = par + 2 * ((n - 1 - par) / 2);
         for (int t = tlast; t >= 0; t -= 2) {
-            const double2 f = fac[t];
+            const auto f = fac[t];
             x = fma(-f.y, x, f.x * row[t]);
             row[t] = x;
         }
     }
     __syncthreads();
-    for (int64_t idx = threadIdx.x; idx < count; idx += blockDim.x) X[base + idx] = tile[(idx / n) * pitch + (idx % n)];
+    for (int li0 = 0; li0 < nl; li0 += kU)
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            T xo[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                xo[u] = (oacc != T(0) && li0 + u < nl) ? X[base + (int64_t)(li0 + u) * n + t] : T(0);
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (li0 + u < nl) {
+                    const T v = oscale * tile[(li0 + u) * pitch + t];
+                    X[base + (int64_t)(li0 + u) * n + t] = (oacc != T(0)) ? fma(oacc, xo[u], v) : v;
+                }
+        }
 }
 
 // G = -F s_i s_j s_k (scale-in) or X = Y s_i s_j s_k (scale-out, sign = +1)
 __global__ void cube_scale_kernel(const double *__restrict__ A, double *__restrict__ B, const double *__restrict__ s,
                                   int n, double sign)
 {
-    const int64_t N = (int64_t)n * n * n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % n), j = (int)((idx / n) % n), i = (int)(idx / ((int64_t)n * n));
+    const int N = n * n * n;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+        const int row = idx / n, k = idx - row * n, i = row / n, j = row - i * n;
         B[idx] = sign * A[idx] * s[i] * s[j] * s[k];
     }
 }
+
+// ---- FP64 defect correction ----
+
+// A~[t, t + dt] for dt in {-2, 0, 2} (the caller keeps t + dt inside [0, n))
+__device__ __forceinline__ double band_coef(const double *d, const double *e, int t, int dt)
+{
+    return dt == 0 ? d[t] : (dt > 0 ? e[t] : e[t - 2]);
+}
+
+__device__ __forceinline__ void block_max_bits(double local, unsigned long long *out)
+{
+    for (int off = 16; off > 0; off >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, off));
+    __shared__ double wmax[32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wmax[w] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bm = 0.0;
+        for (int t = 0; t < (int)(blockDim.x >> 5); ++t) bm = fmax(bm, wmax[t]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(bm));
+    }
+}
+
+// R = G - (T_01 + T_02 + T_12) Y in FP64 (Y read as zero if y_zero); *rmax = max |R|
+// as a bit pattern (must start at 0; NaN and Inf are reported as +Inf).
+__global__ void __launch_bounds__(256) cube_residual_kernel(const double *__restrict__ G, const double *__restrict__ Y,
+                                                            const double *__restrict__ d, const double *__restrict__ e,
+                                                            int n, double *__restrict__ R, bool y_zero,
+                                                            unsigned long long *rmax)
+{
+    const int N = n * n * n;
+    const int nn = n * n;
+    double local = 0.0;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+        double r = G[idx];
+        if (!y_zero) {
+            const int row = idx / n, k = idx - row * n, i = row / n, j = row - i * n;
+            const int idx3[3] = {i, j, k};
+            const int st[3] = {nn, n, 1};
+            double acc = 0.0;
+            // pairs (0,1), (0,2), (1,2): offsets {0, +-2} on both modes of the pair
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+                const int ma = pr == 2 ? 1 : 0, mb = pr == 0 ? 1 : 2;
+                const int ta = idx3[ma], tb = idx3[mb];
+#pragma unroll
+                for (int da = -2; da <= 2; da += 2) {
+                    if (ta + da < 0 || ta + da >= n) continue;
+                    const double ca = band_coef(d, e, ta, da);
+#pragma unroll
+                    for (int db = -2; db <= 2; db += 2) {
+                        if (tb + db < 0 || tb + db >= n) continue;
+                        acc = fma(ca * band_coef(d, e, tb, db), Y[idx + da * st[ma] + db * st[mb]], acc);
+                    }
+                }
+            }
+            r -= acc;
+        }
+        R[idx] = r;
+        const double a = fabs(r);
+        local = (a <= 1.7976931348623157e308) ? fmax(local, a) : __longlong_as_double(0x7ff0000000000000LL);
+    }
+    block_max_bits(local, rmax);
+}
+
+// rho = R / max|R| in FP32
+__global__ void cube_to32_kernel(const double *__restrict__ R, float *__restrict__ rho, int N,
+                                 const unsigned long long *__restrict__ rmax)
+{
+    const double inv = 1.0 / __longlong_as_double((long long)*rmax);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x)
+        rho[idx] = (float)(R[idx] * inv);
+}
+
+// Y = (first ? 0 : Y) + max|R| delta  in FP64
+__global__ void cube_update_kernel(double *__restrict__ Y, const float *__restrict__ delta, int N,
+                                   const unsigned long long *__restrict__ rmax, bool first)
+{
+    const double sc = __longlong_as_double((long long)*rmax);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x)
+        Y[idx] = fma(sc, (double)delta[idx], first ? 0.0 : Y[idx]);
+}
+
+int grid_for(int64_t N) { return (int)std::min<int64_t>((N + 255) / 256, 152 * 16); }
 
 }  // namespace
 
 #define CUBE_CK(call)                                                                                    \
     do {                                                                                                 \
-        cudaError_t e_ = (call);                                                                         \
-        if (e_ != cudaSuccess) {                                                                         \
-            err = std::string(#call) + ": " + cudaGetErrorString(e_);                                    \
+        cudaError_t ce_ = (call);                                                                        \
+        if (ce_ != cudaSuccess) {                                                                        \
+            err = std::string(#call) + ": " + cudaGetErrorString(ce_);                                   \
             return FPS_ERR_CUDA;                                                                         \
         }                                                                                                \
     } while (0)
 
-int CubeEngine::create(int64_t n, double tol, double tol_mid, double tol_in, std::string &err)
+// ===========================================================================
+// CubeNested<T>
+// ===========================================================================
+
+template <typename T>
+int CubeNested<T>::add_stein(double c)
 {
+    Stein s;
+    s.c = c;
+    const double a = -1.0, b = -eps_, d = c / eps_;
+    s.J = adi_iterations(a, b, c, d, tol_in_);
+    zolotarev_shifts(a, b, c, d, s.J, s.p, s.q);
+    s.ab_off = steins_.empty() ? 0 : steins_.back().ab_off + 2 * steins_.back().J + 1;
+    max_sets_ = std::max(max_sets_, 2 * s.J + 1);
+    steins_.push_back(std::move(s));
+    return (int)steins_.size() - 1;
+}
+
+template <typename T>
+int CubeNested<T>::create(int64_t n, double tol, double tol_mid, double tol_in, bool residual, std::string &err)
+{
+    residual_ = residual;
     n_ = n;
     tol_ = tol;
     tol_mid_ = tol_mid;
     tol_in_ = tol_in;
     eps_ = square_eps(n);
-    std::vector<double> d, e, s;
+    // the schedule of every level, fixed for the plan
+    const double e2 = eps_ * eps_;
+    J_outer = adi_iterations(-1.0, -e2, 2 * e2, 2.0, tol_);
+    std::vector<double> pp, qq;
+    zolotarev_shifts(-1.0, -e2, 2 * e2, 2.0, J_outer, pp, qq);
+    inner_per_run = 0;
+    for (int j = 0; j < J_outer; ++j) {
+        Outer o;
+        o.p = qq[j];  // in sigma(H)'s interval [2 eps^2, 2]
+        o.q = pp[j];  // in sigma(-V)'s interval [-1, -eps^2]
+        o.stein_v = add_stein(o.p);
+        inner_per_run += (residual_ ? 2 : 1) * steins_[o.stein_v].J;
+        const double s = -o.q, lo = e2 + s / 2, hi = 1.0 + s / 2;
+        const int Jm = adi_iterations(-hi, -lo, lo, hi, tol_mid_);
+        std::vector<double> am;
+        zolotarev_shifts_symmetric(lo, hi, Jm, am);
+        for (int m = 0; m < Jm; ++m) {
+            Middle mid;
+            mid.a = am[m];
+            mid.stein = add_stein(s / 2 + am[m]);
+            inner_per_run += (residual_ && m + 1 < Jm ? 3 : 2) * steins_[mid.stein].J;
+            o.mid.push_back(mid);
+        }
+        outer_.push_back(std::move(o));
+    }
+    std::vector<double2> hab;
+    for (const Stein &s : steins_) {
+        hab.push_back(make_double2(1.0, 0.0));
+        for (int l = 0; l < s.J; ++l) {
+            hab.push_back(make_double2(s.p[l], s.c));
+            hab.push_back(make_double2(1.0, -s.q[l]));
+        }
+    }
+    std::vector<double> d, e;
     square_bands(n, d, e);
-    inv_sqrt_E(n, s);
+    std::vector<T> dT(d.begin(), d.end()), eT(e.begin(), e.end());
     const size_t N = (size_t)n * n * n;
-    auto alloc = [&](double **p, size_t cnt) -> cudaError_t {
-        cudaError_t r = cudaMalloc((void **)p, sizeof(double) * (cnt ? cnt : 1));
+    auto alloc = [&](void **p, size_t b) -> cudaError_t {
+        cudaError_t r = cudaMalloc(p, b ? b : 1);
         if (r == cudaSuccess) {
             allocs_.push_back(*p);
-            bytes += (int64_t)(sizeof(double) * cnt);
+            bytes += (int64_t)b;
         }
         return r;
     };
-    CUBE_CK(alloc(&bd_, n));
-    CUBE_CK(alloc(&be_, n));
-    CUBE_CK(alloc(&bs_, n));
-    for (double *&w : work_) CUBE_CK(alloc(&w, N));
-    // factor sets: the constant A~ and two per inner iteration
-    max_sets_ = 2 * 512 + 1;
-    CUBE_CK(cudaMalloc((void **)&fac_, sizeof(double2) * (size_t)max_sets_ * n));
-    CUBE_CK(cudaMalloc((void **)&ab_, sizeof(double2) * (size_t)max_sets_));
-    CUBE_CK(cudaMallocHost((void **)&h_ab_, sizeof(double2) * (size_t)max_sets_));
-    bytes += (int64_t)(sizeof(double2) * (size_t)max_sets_ * (n + 1));
-    CUBE_CK(cudaMemcpy(bd_, d.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    CUBE_CK(cudaMemcpy(be_, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    CUBE_CK(cudaMemcpy(bs_, s.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    const int smem = kLines * (int)(n + 1) * (int)sizeof(double);
-    CUBE_CK(cudaFuncSetAttribute(cube_solve_contig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const double e2 = eps_ * eps_;
-    J_outer = adi_iterations(-1.0, -e2, 2 * e2, 2.0, tol_);
+    CUBE_CK(alloc((void **)&bd64_, sizeof(double) * n));
+    CUBE_CK(alloc((void **)&be64_, sizeof(double) * n));
+    CUBE_CK(alloc((void **)&bd_, sizeof(T) * n));
+    CUBE_CK(alloc((void **)&be_, sizeof(T) * n));
+    const int nwork = residual_ ? 11 : 8;
+    for (int w = 0; w < nwork; ++w) CUBE_CK(alloc((void **)&work_[w], sizeof(T) * N));
+    CUBE_CK(alloc(&fac_, sizeof(typename V2<T>::type) * (size_t)max_sets_ * n));
+    CUBE_CK(alloc((void **)&ab_, sizeof(double2) * hab.size()));
+    CUBE_CK(cudaMemcpy(bd64_, d.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CUBE_CK(cudaMemcpy(be64_, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CUBE_CK(cudaMemcpy(bd_, dT.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
+    CUBE_CK(cudaMemcpy(be_, eT.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
+    CUBE_CK(cudaMemcpy(ab_, hab.data(), sizeof(double2) * hab.size(), cudaMemcpyHostToDevice));
+    CUBE_CK(cudaFuncSetAttribute(cube_solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kLines * contig_pitch((int)n) * (int)sizeof(T)));
+    CUBE_CK(cudaFuncSetAttribute(cube_solve_strided_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * (int)((n + 1) / 2) * kLines * (int)sizeof(T)));
+    fac_entry_ = -1;
     return FPS_OK;
 }
 
-void CubeEngine::release()
+template <typename T>
+void CubeNested<T>::release()
 {
-    for (double *p : allocs_) cudaFree(p);
+    for (void *p : allocs_) cudaFree(p);
     allocs_.clear();
-    if (fac_) cudaFree(fac_);
-    if (ab_) cudaFree(ab_);
-    if (h_ab_) cudaFreeHost(h_ab_);
-    fac_ = nullptr;
-    ab_ = nullptr;
-    h_ab_ = nullptr;
 }
 
-// ---- launch helpers (all asynchronous on st_) ----
-cudaError_t CubeEngine::band(const double *X, const double *R, double *Y, int mode, double alpha, double beta,
-                             double sop, double sr)
+template <typename T>
+cudaError_t CubeNested<T>::band(const T *X, const T *R, T *Y, int mode, double alpha, double beta, double sop,
+                                double sr)
 {
     const int64_t N = n_ * n_ * n_;
-    int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
-    cube_band_kernel<<<blocks, 256, 0, st_>>>(X, R, Y, bd_, be_, (int)n_, mode, alpha, beta, sop, sr);
-    ++launches_last;
+    cube_band_kernel<T><<<grid_for(N), 256, 0, st_>>>(X, R, Y, bd_, be_, (int)n_, mode, (T)alpha, (T)beta, (T)sop,
+                                                       (T)sr);
+    ++launches;
     return cudaGetLastError();
 }
 
-cudaError_t CubeEngine::axpby(const double *X, const double *Y, double *Z, double a, double b)
+template <typename T>
+cudaError_t CubeNested<T>::axpby(const T *X, const T *Y, T *Z, double a, double b)
 {
     const int64_t N = n_ * n_ * n_;
-    int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
-    cube_axpby_kernel<<<blocks, 256, 0, st_>>>(X, Y, Z, N, a, b);
-    ++launches_last;
+    cube_axpby_kernel<T><<<grid_for(N), 256, 0, st_>>>(X, Y, Z, (int)N, (T)a, (T)b);
+    ++launches;
     return cudaGetLastError();
 }
 
-cudaError_t CubeEngine::solve(int set, const double *R1, double s1, const double *R2, double s2, double *X, int mode)
+template <typename T>
+cudaError_t CubeNested<T>::axpy3(const T *X, const T *Y, const T *W, T *V, double a, double b, double c)
 {
-    const double2 *fac = fac_ + (int64_t)set * n_;
+    const int64_t N = n_ * n_ * n_;
+    cube_axpy3_kernel<T><<<grid_for(N), 256, 0, st_>>>(X, Y, W, V, (int)N, (T)a, (T)b, (T)c);
+    ++launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t CubeNested<T>::solve(int set, const T *R1, double s1, const T *R2, double s2, T *X, int mode,
+                                 double oscale, double oacc)
+{
+    using F2 = typename V2<T>::type;
+    const F2 *fac = reinterpret_cast<const F2 *>(fac_) + (int64_t)set * n_;
     if (mode == 2) {
         const int64_t nlines = n_ * n_;
         const int blocks = (int)((nlines + kLines - 1) / kLines);
-        const int smem = kLines * (int)(n_ + 1) * (int)sizeof(double);
-        cube_solve_contig_kernel<<<blocks, 2 * kLines, smem, st_>>>(fac, R1, s1, R2, s2, X, (int)n_);
+        const int smem = kLines * contig_pitch((int)n_) * (int)sizeof(T);
+        cube_solve_contig_kernel<T><<<blocks, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, (int)n_,
+                                                                        (T)oscale, (T)oacc);
     } else {
-        const int64_t threads = 2 * n_ * n_;
-        cube_solve_strided_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st_>>>(fac, R1, s1, R2, s2, X, (int)n_,
-                                                                                       mode);
+        const int nkb = (int)((n_ + kLines - 1) / kLines);
+        const int smem = 2 * (int)((n_ + 1) / 2) * kLines * (int)sizeof(T);
+        cube_solve_strided_kernel<T><<<(unsigned)(n_ * nkb), 2 * kLines, smem, st_>>>(
+            fac, R1, (T)s1, R2, (T)s2, X, (int)n_, mode, (T)oscale, (T)oacc);
     }
-    ++launches_last;
+    ++launches;
     return cudaGetLastError();
 }
 
-// Z = (T_ab + c)^{-1} R, the inner level.  Uses work_[6], work_[7].
-int CubeEngine::stein(int ma, int mb, double c, const double *R, double *Z, std::string &err)
+template <typename T>
+int CubeNested<T>::load_factors(int entry, std::string &err)
 {
-    const double a = -1.0, b = -eps_, cc = c, d = c / eps_;
-    const int J = adi_iterations(a, b, cc, d, tol_in_);
-    if (2 * J + 1 > max_sets_) {
-        err = "inner iteration count exceeds the factor table";
-        return FPS_ERR_UNSUPPORTED;
-    }
-    std::vector<double> p, q;
-    zolotarev_shifts(a, b, cc, d, J, p, q);
-    // factor sets: 0 = A~ (alpha 1, beta 0); 1 + 2l = c + p_l A~; 2 + 2l = A~ - q_l
-    CUBE_CK(cudaStreamSynchronize(st_));  // the pinned staging of the previous call must be consumed
-    h_ab_[0] = make_double2(1.0, 0.0);
-    for (int l = 0; l < J; ++l) {
-        h_ab_[1 + 2 * l] = make_double2(p[l], c);
-        h_ab_[2 + 2 * l] = make_double2(1.0, -q[l]);
-    }
-    const int nsets = 2 * J + 1;
-    CUBE_CK(cudaMemcpyAsync(ab_, h_ab_, sizeof(double2) * nsets, cudaMemcpyHostToDevice, st_));
-    cube_factor_kernel<<<(2 * nsets + 127) / 128, 128, 0, st_>>>(bd_, be_, (int)n_, ab_, nsets, fac_);
-    ++launches_last;
+    if (fac_entry_ == entry) return FPS_OK;
+    const Stein &S = steins_[entry];
+    const int nsets = 2 * S.J + 1;
+    // factor sets: 0 = A~; 1 + 2l = c + p_l A~; 2 + 2l = A~ - q_l
+    cube_factor_kernel<T><<<(2 * nsets + 127) / 128, 128, 0, st_>>>(bd64_, be64_, (int)n_, ab_ + S.ab_off, nsets,
+                                                                     reinterpret_cast<typename V2<T>::type *>(fac_));
+    ++launches;
     CUBE_CK(cudaGetLastError());
-    double *W1 = work_[6], *W2 = work_[7];
-    for (int l = 0; l < J; ++l) {
-        const double *U = R;
-        if (l > 0) {
-            CUBE_CK(band(Z, nullptr, W1, mb, 1.0, 0.0, 1.0, 0.0));         // Z A~_b
-            CUBE_CK(band(W1, R, W2, ma, 1.0, -p[l], -1.0, 1.0));           // R - (A~_a - p) ( . )
-            U = W2;
-        }
-        CUBE_CK(solve(1 + 2 * l, U, 1.0, nullptr, 0.0, W1, mb));           // Z_h = ( . ) (c + p A~_b)^{-1}
-        CUBE_CK(solve(0, R, 1.0, W1, -c, W2, mb));                          // (R - c Z_h) A~_b^{-1}
-        CUBE_CK(solve(2 + 2 * l, W2, 1.0, W1, -q[l], Z, ma));               // (A~_a - q)^{-1} ( . - q Z_h)
-    }
-    inner_iters += J;
+    fac_entry_ = entry;
     return FPS_OK;
 }
 
-// Y = (T_01 + T_02 + s)^{-1} R, the middle level.  Uses work_[3..5].
-int CubeEngine::hsolve(double s, const double *R, double *Y, std::string &err)
+// Z = (T_ab + c)^{-1} R, the inner level in the paper's form (entry = schedule
+// index).  Uses work_[0], work_[1].
+template <typename T>
+int CubeNested<T>::stein(int ma, int mb, int entry, const T *R, T *Z, std::string &err)
 {
-    const double lo = eps_ * eps_ + s / 2, hi = 1.0 + s / 2;
-    const int J = adi_iterations(-hi, -lo, lo, hi, tol_mid_);
-    std::vector<double> am;
-    zolotarev_shifts_symmetric(lo, hi, J, am);
-    double *Wh = work_[3], *T1 = work_[4], *T2 = work_[5];
-    CUBE_CK(cudaMemsetAsync(Y, 0, sizeof(double) * n_ * n_ * n_, st_));
-    for (int m = 0; m < J; ++m) {
-        const double a = am[m];
-        // T1 = R - (T_01 + s/2 - a) Y
-        CUBE_CK(band(Y, nullptr, T1, 0, 1.0, 0.0, 1.0, 0.0));
-        CUBE_CK(band(T1, R, T2, 1, 1.0, 0.0, -1.0, 1.0));
-        CUBE_CK(axpby(T2, Y, T1, 1.0, -(s / 2 - a)));
-        int st = stein(0, 2, s / 2 + a, T1, Wh, err);
+    int st = load_factors(entry, err);
+    if (st != FPS_OK) return st;
+    const Stein &S = steins_[entry];
+    T *W1 = work_[0], *W2 = work_[1];
+    const double c = S.c;
+    for (int l = 0; l < S.J; ++l) {
+        const T *U = R;
+        if (l > 0) {
+            CUBE_CK(band(Z, nullptr, W1, mb, 1.0, 0.0, 1.0, 0.0));                // Z A~_b
+            CUBE_CK(band(W1, R, W2, ma, 1.0, -S.p[l], -1.0, 1.0));                // R - (A~_a - p) ( . )
+            U = W2;
+        }
+        CUBE_CK(solve(1 + 2 * l, U, 1.0, nullptr, 0.0, W1, mb, 1.0, 0.0));      // Z_h = ( . ) (c + p A~_b)^{-1}
+        CUBE_CK(solve(0, R, 1.0, W1, -c, W2, mb, 1.0, 0.0));                     // (R - c Z_h) A~_b^{-1}
+        CUBE_CK(solve(2 + 2 * l, W2, 1.0, W1, -S.q[l], Z, ma, 1.0, 0.0));        // (A~_a - q)^{-1} ( . - q Z_h)
+    }
+    return FPS_OK;
+}
+
+// Y = (T_01 + T_02 + s)^{-1} R with s = -o.q, the middle level in the paper's
+// form.  Uses work_[2..4].
+template <typename T>
+int CubeNested<T>::hsolve(const Outer &o, const T *R, T *Y, std::string &err)
+{
+    const double s = -o.q;
+    T *Wh = work_[2], *T1 = work_[3], *T2 = work_[4];
+    for (size_t m = 0; m < o.mid.size(); ++m) {
+        const double a = o.mid[m].a;
+        const T *U = R;  // R - (T_01 + s/2 - a) Y, with Y = 0 at m = 0
+        if (m > 0) {
+            CUBE_CK(band(Y, nullptr, T1, 0, 1.0, 0.0, 1.0, 0.0));
+            CUBE_CK(band(T1, R, T2, 1, 1.0, 0.0, -1.0, 1.0));
+            CUBE_CK(axpby(T2, Y, T1, 1.0, -(s / 2 - a)));
+            U = T1;
+        }
+        int st = stein(0, 2, o.mid[m].stein, U, Wh, err);
         if (st != FPS_OK) return st;
         // T1 = R - (T_02 + s/2 - a) Wh
         CUBE_CK(band(Wh, nullptr, T1, 0, 1.0, 0.0, 1.0, 0.0));
         CUBE_CK(band(T1, R, T2, 2, 1.0, 0.0, -1.0, 1.0));
         CUBE_CK(axpby(T2, Wh, T1, 1.0, -(s / 2 - a)));
-        st = stein(0, 1, s / 2 + a, T1, Y, err);
+        st = stein(0, 1, o.mid[m].stein, T1, Y, err);
         if (st != FPS_OK) return st;
     }
     return FPS_OK;
 }
 
-int CubeEngine::solve_cube(const double *F, double *X, cudaStream_t st, std::string &err)
+// The inner level with its residual carried.  The slice equation is the Sylvester
+// equation A Z - Z B = C with A = A~_a, B = -c A~_b^{-1}, C = R A~_b^{-1}; with
+// rho = C - A Z + Z B the two half-steps of Algorithm 2 become
+//   rho+ = (A - q)^{-1} (A - p) rho (B - p)^{-1} (B - q),
+//   Z+   = Z + (q - p) (A - q)^{-1} rho (B - p)^{-1},
+// and rho (B - p)^{-1} = -rho A~_b (c + p A~_b)^{-1}.  Per iteration: one product and
+// one solve along b, two solves along a.  Uses work_[0..2].
+template <typename T>
+int CubeNested<T>::stein_res(int ma, int mb, int entry, const T *R, T *Z, std::string &err)
+{
+    int st = load_factors(entry, err);
+    if (st != FPS_OK) return st;
+    const Stein &S = steins_[entry];
+    T *rho = work_[0], *a1 = work_[1], *g = work_[2];
+    CUBE_CK(solve(0, R, 1.0, nullptr, 0.0, rho, mb, 1.0, 0.0));                 // rho = R A~_b^{-1}
+    for (int l = 0; l < S.J; ++l) {
+        const double p = S.p[l], q = S.q[l];
+        const T *t = R;                                                          // rho A~_b (= R at l = 0)
+        if (l > 0) {
+            CUBE_CK(band(rho, nullptr, a1, mb, 1.0, 0.0, 1.0, 0.0));
+            t = a1;
+        }
+        CUBE_CK(solve(1 + 2 * l, t, -1.0, nullptr, 0.0, a1, mb, 1.0, 0.0));     // a1 = rho (B - p)^{-1}
+        if (l + 1 < S.J) {
+            // rho+ = c1 + (q - p)(A - q)^{-1} c1 with c1 = rho + (p - q) a1
+            CUBE_CK(solve(2 + 2 * l, rho, 1.0, a1, p - q, g, ma, 1.0, 0.0));
+            CUBE_CK(axpy3(rho, a1, g, rho, 1.0, p - q, q - p));
+        }
+        // Z += (q - p)(A - q)^{-1} a1
+        CUBE_CK(solve(2 + 2 * l, a1, 1.0, nullptr, 0.0, Z, ma, q - p, l == 0 ? 0.0 : 1.0));
+    }
+    return FPS_OK;
+}
+
+// The middle level with its residual carried: for A' W + B' W = R (A' = T_01 + s/2,
+// B' = T_02 + s/2) and shifts +-a,
+//   rho+ = [I - 2a (A' + a)^{-1}] [I - 2a (B' + a)^{-1}] rho,
+//   W+   = W + (A' + a)^{-1} 2a (B' + a)^{-1} rho,
+// three slice Stein solves per iteration (two in the last).  Uses work_[3..6].
+template <typename T>
+int CubeNested<T>::hsolve_res(const Outer &o, const T *R, T *W, std::string &err)
+{
+    T *rho = work_[3], *v = work_[4], *c2 = work_[5], *g = work_[6];
+    const size_t J = o.mid.size();
+    for (size_t m = 0; m < J; ++m) {
+        const double a = o.mid[m].a;
+        const int entry = o.mid[m].stein;
+        const T *r = (m == 0) ? R : rho;
+        int st = stein_res(0, 2, entry, r, v, err);                          // v = (B' + a)^{-1} rho
+        if (st != FPS_OK) return st;
+        if (m + 1 < J) {
+            CUBE_CK(axpby(r, v, c2, 1.0, -2.0 * a));                         // c2 = rho - 2a v
+            st = stein_res(0, 1, entry, c2, g, err);                         // g = (A' + a)^{-1} c2
+            if (st != FPS_OK) return st;
+            CUBE_CK(axpby(c2, g, rho, 1.0, -2.0 * a));                       // rho+ = c2 - 2a g
+        }
+        CUBE_CK(axpby(v, v, c2, 2.0 * a, 0.0));                              // 2a v
+        st = stein_res(0, 1, entry, c2, g, err);                             // (A' + a)^{-1} 2a v
+        if (st != FPS_OK) return st;
+        if (m == 0) CUBE_CK(axpby(g, g, W, 1.0, 0.0));
+        else CUBE_CK(axpby(W, g, W, 1.0, 1.0));
+    }
+    return FPS_OK;
+}
+
+// The outer level with the residual rho = G - (H + V) Y carried instead of Y's
+// right-hand sides.  The two half-steps of (5.3)-(5.4) are Y_h = Y + (V + p)^{-1} rho
+// and Y+ = Y_h + (H - q)^{-1} rho_h, so that, the operators commuting,
+//   rho+ = [I + (q - p)(V + p)^{-1}] [I + (q - p)(H - q)^{-1}] rho,
+//   Y+   = Y + (V + p)^{-1} (p - q) (H - q)^{-1} rho:
+// only residuals are solved with and no product with H or V of a growing iterate
+// is formed, which keeps FP32 rounding relative to the residual (the paper's form
+// loses it to cancellation at small shifts).  Uses work_[7..10].
+template <typename T>
+int CubeNested<T>::run_residual(const T *G, T *Y, std::string &err)
+{
+    T *rho = work_[7], *w = work_[8], *cb = work_[9], *u = work_[10];
+    for (int j = 0; j < J_outer; ++j) {
+        const Outer &o = outer_[j];
+        const T *r = (j == 0) ? G : rho;
+        int s = hsolve_res(o, r, w, err);                               // w = (H - q)^{-1} rho
+        if (s != FPS_OK) return s;
+        CUBE_CK(axpby(r, w, cb, 1.0, o.q - o.p));                       // c = rho + (q - p) w
+        s = stein_res(1, 2, o.stein_v, cb, u, err);                     // u = (V + p)^{-1} c
+        if (s != FPS_OK) return s;
+        CUBE_CK(axpby(cb, u, rho, 1.0, o.q - o.p));                     // rho+ = c + (q - p) u
+        // the scalar p - q goes in before the solve: w ~ rho / eps^2 and
+        // (V + p)^{-1} w ~ rho / eps^4 would leave the FP32 range for n >~ 100
+        CUBE_CK(axpby(w, w, cb, o.p - o.q, 0.0));
+        s = stein_res(1, 2, o.stein_v, cb, u, err);                     // b = (V + p)^{-1} (p - q) w
+        if (s != FPS_OK) return s;
+        if (j == 0) CUBE_CK(axpby(u, u, Y, 1.0, 0.0));                  // Y = b
+        else CUBE_CK(axpby(Y, u, Y, 1.0, 1.0));                         // Y += b
+    }
+    return FPS_OK;
+}
+
+template <typename T>
+int CubeNested<T>::run(const T *G, T *Y, cudaStream_t st, std::string &err)
 {
     st_ = st;
-    inner_iters = 0;
-    launches_last = 0;
-    const int64_t N = n_ * n_ * n_;
-    double *G = work_[0], *Y = work_[1], *Yh = work_[2], *T1 = work_[8], *T2 = work_[9];
-    {
-        int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
-        cube_scale_kernel<<<blocks, 256, 0, st_>>>(F, G, bs_, (int)n_, -1.0);
-        ++launches_last;
-        CUBE_CK(cudaGetLastError());
-    }
-    const double e2 = eps_ * eps_;
-    std::vector<double> pp, qq;
-    zolotarev_shifts(-1.0, -e2, 2 * e2, 2.0, J_outer, pp, qq);
-    CUBE_CK(cudaMemsetAsync(Y, 0, sizeof(double) * N, st_));
+    launches = 0;
+    if (residual_) return run_residual(G, Y, err);
+    T *Yh = work_[5], *T1 = work_[6], *T2 = work_[7];
     for (int j = 0; j < J_outer; ++j) {
-        const double p = qq[j], q = pp[j];  // p in sigma(H)'s interval, q in sigma(-V)'s
-        // T1 = G - (H - p) Y = G - T_01 Y - T_02 Y + p Y
-        CUBE_CK(band(Y, nullptr, T2, 0, 1.0, 0.0, 1.0, 0.0));      // A~_0 Y
-        CUBE_CK(band(T2, G, T1, 1, 1.0, 0.0, -1.0, 1.0));          // G - T_01 Y
-        CUBE_CK(band(T2, T1, T1, 2, 1.0, 0.0, -1.0, 1.0));         // ... - T_02 Y  (T1 read before written, element-wise)
-        CUBE_CK(axpby(T1, Y, T1, 1.0, p));
-        int s = stein(1, 2, p, T1, Yh, err);
+        const Outer &o = outer_[j];
+        const T *U = G;  // G - (H - p) Y, with Y = 0 at j = 0
+        if (j > 0) {
+            CUBE_CK(band(Y, nullptr, T2, 0, 1.0, 0.0, 1.0, 0.0));      // A~_0 Y
+            CUBE_CK(band(T2, G, T1, 1, 1.0, 0.0, -1.0, 1.0));          // G - T_01 Y
+            CUBE_CK(band(T2, T1, T1, 2, 1.0, 0.0, -1.0, 1.0));         // ... - T_02 Y (element-wise in place)
+            CUBE_CK(axpby(T1, Y, T1, 1.0, o.p));
+            U = T1;
+        }
+        int s = stein(1, 2, o.stein_v, U, Yh, err);
         if (s != FPS_OK) return s;
         // T1 = G - (V + q) Y_h = G - T_12 Y_h - q Y_h
         CUBE_CK(band(Yh, nullptr, T2, 1, 1.0, 0.0, 1.0, 0.0));
         CUBE_CK(band(T2, G, T1, 2, 1.0, 0.0, -1.0, 1.0));
-        CUBE_CK(axpby(T1, Yh, T1, 1.0, -q));
-        s = hsolve(-q, T1, Y, err);
+        CUBE_CK(axpby(T1, Yh, T1, 1.0, -o.q));
+        s = hsolve(o, T1, Y, err);
         if (s != FPS_OK) return s;
     }
-    {
-        int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
-        cube_scale_kernel<<<blocks, 256, 0, st_>>>(Y, X, bs_, (int)n_, 1.0);
-        ++launches_last;
-        CUBE_CK(cudaGetLastError());
+    return FPS_OK;
+}
+
+template class CubeNested<double>;
+template class CubeNested<float>;
+
+// ===========================================================================
+// CubeEngine
+// ===========================================================================
+
+int CubeEngine::create(int64_t n, double tol, int precision, std::string &err)
+{
+    n_ = n;
+    tol_ = tol;
+    precision_ = precision;
+    std::vector<double> d, e, s;
+    square_bands(n, d, e);
+    inv_sqrt_E(n, s);
+    const size_t N = (size_t)n * n * n;
+    auto alloc = [&](void **p, size_t b) -> cudaError_t {
+        cudaError_t r = cudaMalloc(p, b ? b : 1);
+        if (r == cudaSuccess) {
+            allocs_.push_back(*p);
+            bytes += (int64_t)b;
+        }
+        return r;
+    };
+    CUBE_CK(alloc((void **)&bd_, sizeof(double) * n));
+    CUBE_CK(alloc((void **)&be_, sizeof(double) * n));
+    CUBE_CK(alloc((void **)&bs_, sizeof(double) * n));
+    CUBE_CK(alloc((void **)&G_, sizeof(double) * N));
+    CUBE_CK(alloc((void **)&Y_, sizeof(double) * N));
+    CUBE_CK(cudaMemcpy(bd_, d.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CUBE_CK(cudaMemcpy(be_, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CUBE_CK(cudaMemcpy(bs_, s.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    int st;
+    if (precision == FPS_FP64) {
+        n64_ = new CubeNested<double>();
+        st = n64_->create(n, tol, 1e-15, 1e-15, false, err);
+        if (st != FPS_OK) return st;
+        J_outer = n64_->J_outer;
+        bytes += n64_->bytes;
+    } else {
+        CUBE_CK(alloc((void **)&R_, sizeof(double) * N));
+        CUBE_CK(alloc((void **)&rho_, sizeof(float) * N));
+        CUBE_CK(alloc((void **)&delta_, sizeof(float) * N));
+        CUBE_CK(alloc((void **)&d_max_, sizeof(unsigned long long)));
+        CUBE_CK(cudaMallocHost((void **)&h_max_, sizeof(unsigned long long)));
+        n32_ = new CubeNested<float>();
+        st = n32_->create(n, kRefTol, kRefTolMid, kRefTolIn, true, err);
+        if (st != FPS_OK) return st;
+        J_outer = J_outer_inner = n32_->J_outer;
+        bytes += n32_->bytes;
     }
+    return FPS_OK;
+}
+
+void CubeEngine::release()
+{
+    if (n64_) {
+        n64_->release();
+        delete n64_;
+        n64_ = nullptr;
+    }
+    if (n32_) {
+        n32_->release();
+        delete n32_;
+        n32_ = nullptr;
+    }
+    for (void *p : allocs_) cudaFree(p);
+    allocs_.clear();
+    if (h_max_) cudaFreeHost(h_max_);
+    h_max_ = nullptr;
+}
+
+int CubeEngine::solve_cube(const double *F, double *X, cudaStream_t st, std::string &err)
+{
+    inner_iters = 0;
+    launches_last = 0;
+    rounds_last = 0;
+    resid_last = 0.0;
+    const int64_t N = n_ * n_ * n_;
+    cube_scale_kernel<<<grid_for(N), 256, 0, st>>>(F, G_, bs_, (int)n_, -1.0);
+    ++launches_last;
+    CUBE_CK(cudaGetLastError());
+    if (precision_ == FPS_FP64) {
+        const int s = n64_->run(G_, Y_, st, err);
+        launches_last += n64_->launches;
+        if (s != FPS_OK) return s;
+        inner_iters = n64_->inner_per_run;
+    } else {
+        double gmax = 0.0;
+        int status = FPS_ERR_NOT_CONVERGED;
+        for (int r = 0; r <= max_rounds; ++r) {
+            CUBE_CK(cudaMemsetAsync(d_max_, 0, sizeof(unsigned long long), st));
+            cube_residual_kernel<<<grid_for(N), 256, 0, st>>>(G_, Y_, bd_, be_, (int)n_, R_, r == 0, d_max_);
+            ++launches_last;
+            CUBE_CK(cudaGetLastError());
+            CUBE_CK(cudaMemcpyAsync(h_max_, d_max_, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            CUBE_CK(cudaStreamSynchronize(st));
+            const unsigned long long bits = *h_max_;
+            double rmax;
+            std::memcpy(&rmax, &bits, sizeof(double));
+            if (!std::isfinite(rmax)) {
+                err = "non-finite right-hand side or residual";
+                return FPS_ERR_NONFINITE;
+            }
+            if (r == 0) {
+                gmax = rmax;
+                if (gmax == 0.0) {
+                    CUBE_CK(cudaMemsetAsync(Y_, 0, sizeof(double) * N, st));
+                    status = FPS_OK;
+                    break;
+                }
+            }
+            resid_last = rmax / gmax;
+            if (r > 0 && resid_last <= tol_) {
+                status = FPS_OK;
+                break;
+            }
+            if (r == max_rounds) break;
+            cube_to32_kernel<<<grid_for(N), 256, 0, st>>>(R_, rho_, (int)N, d_max_);
+            ++launches_last;
+            CUBE_CK(cudaGetLastError());
+            const int s = n32_->run(rho_, delta_, st, err);
+            launches_last += n32_->launches;
+            if (s != FPS_OK) return s;
+            cube_update_kernel<<<grid_for(N), 256, 0, st>>>(Y_, delta_, (int)N, d_max_, r == 0);
+            ++launches_last;
+            CUBE_CK(cudaGetLastError());
+            inner_iters += n32_->inner_per_run;
+            rounds_last = r + 1;
+        }
+        if (status != FPS_OK) {
+            cube_scale_kernel<<<grid_for(N), 256, 0, st>>>(Y_, X, bs_, (int)n_, 1.0);
+            ++launches_last;
+            err = "refinement did not reach the tolerance";
+            return status;
+        }
+    }
+    cube_scale_kernel<<<grid_for(N), 256, 0, st>>>(Y_, X, bs_, (int)n_, 1.0);
+    ++launches_last;
+    CUBE_CK(cudaGetLastError());
     return FPS_OK;
 }
 

@@ -268,8 +268,6 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     if (precision != FPS_FP64 && precision != FPS_FP32_REFINE)
         return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: unknown precision");
     if (dim == 3) {
-        if (precision != FPS_FP64)
-            return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the cube runs in FPS_FP64 only");
         if (n > 320) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the cube supports n <= 320");
         fps_plan *p = new fps_plan();
         p->n = n;
@@ -285,7 +283,7 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
         }
         p->cube = new fps::CubeEngine();
         std::string err;
-        const int st = p->cube->create(n, tol, 1e-15, 1e-15, err);
+        const int st = p->cube->create(n, tol, precision, err);
         if (st != FPS_OK) {
             release(p);
             return fail(st, "fps_plan_create: " + err);
@@ -483,6 +481,12 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->J_inner = plan->eng ? plan->eng->J_inner_first : 0;
     info->refine_rounds = plan->eng ? plan->eng->rounds_last : 0;
     info->last_residual = plan->eng ? plan->eng->resid_last : 0.0;
+    if (plan->cube) {
+        info->J_inner = plan->cube->J_outer_inner;
+        info->refine_rounds = plan->cube->rounds_last;
+        info->last_residual = plan->cube->resid_last;
+        info->inner_iterations = plan->cube->inner_iters;
+    }
     info->tol = plan->tol;
     info->device_bytes = plan->bytes;
     info->kernel_launches = plan->launches_last;
