@@ -40,7 +40,7 @@ namespace fps {
 namespace {
 
 constexpr int kLines = 32;  // lines per CTA of the solve kernels
-constexpr int kU = 8;       // rows of global loads in flight per thread in the solve kernels
+constexpr int kU = 8;       // global loads in flight per thread in the solve output phase
 
 template <typename T>
 struct V2;
@@ -111,146 +111,191 @@ __global__ void cube_factor_kernel(const double *__restrict__ d, const double *_
     }
 }
 
-// X = oscale (alpha A~ + beta)^{-1} (s1 R1 + s2 R2) + oacc X along mode 0 or 1
-// (oacc = 0: X is not read).  X may alias R1/R2 when oacc = 0: each element is
-// read and written by one thread, the read first.
-// CTA = 2 warps over kLines lines adjacent in mode 2: warp = parity, lane = line,
-// so every load and store of a step is one coalesced row of the tensor.  The
-// forward sweep reads kU rows ahead of the recurrence and keeps its z values in
-// shared memory for the backward sweep, which writes X directly.
-// Grid: one CTA per (index of the other strided mode, block of kLines in mode 2).
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Asynchronous copy of one element (4 or 8 bytes) from global to shared memory.
 template <typename T>
-__global__ void __launch_bounds__(64) cube_solve_strided_kernel(const typename V2<T>::type *__restrict__ fac,
-                                                                const T *R1, T s1, const T *R2, T s2, T *X, int n,
-                                                                int mode, T oscale, T oacc)
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
 {
+    if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// Shared-memory row pitch of a contiguous-mode tile: odd, so that the 32 lanes of a
+// warp (one line each, same t) hit distinct banks.
+__host__ __device__ __forceinline__ int contig_pitch(int n) { return (n % 2 == 0) ? n + 1 : n + 2; }
+
+// Elements of one shared-memory tile of the line solve.
+__host__ __device__ __forceinline__ int line_tile_elems(int n, bool contig)
+{
+    return contig ? kLines * contig_pitch(n) : kLines * n;
+}
+
+// Dynamic shared memory of the line solve: the factor set and two tiles.
+template <typename T>
+int line_smem_bytes(int n, bool contig)
+{
+    return n * (int)sizeof(typename V2<T>::type) + 2 * line_tile_elems(n, contig) * (int)sizeof(T);
+}
+
+// Banded solves along one mode for kLines lines per CTA:
+//   IN = s1 R1 + s2 R2            (preband: IN = s1 (A~ R1) along the mode, R2 unused)
+//   X  = oscale (alpha A~ + beta)^{-1} IN + oin IN + oacc X      (X read only if oacc != 0)
+// The whole tile of R1 (and R2) is fetched with asynchronous copies, so one CTA has
+// all its bytes in flight at once; the input combination and both Thomas sweeps
+// (App. B parity decoupling: warp = parity, lane = line) run in shared memory, and
+// the output combination is written back coalesced.  X may alias R1 or R2.
+// CONTIG (mode 2): kLines consecutive lines, tile [line][t].  Otherwise (modes 0,
+// 1): kLines lines adjacent in mode 2, one CTA per (index of the other strided mode,
+// block of kLines), tile [t][line].
+template <typename T, bool CONTIG>
+__global__ void __launch_bounds__(64) cube_line_kernel(const typename V2<T>::type *__restrict__ fac, const T *R1,
+                                                       T s1, const T *R2, T s2, T *X, int n, int mode, T oscale,
+                                                       T oin, T oacc, bool preband, const T *__restrict__ d,
+                                                       const T *__restrict__ e)
+{
+    using F2 = typename V2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int half = (n + 1) / 2;
-    const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
-    T *zs = reinterpret_cast<T *>(smem_raw) + par * half * kLines;  // [half][kLines] of this parity
-    const int nkb = (n + kLines - 1) / kLines;
-    const int other = blockIdx.x / nkb, k0 = (blockIdx.x % nkb) * kLines;
-    const bool act = k0 + lane < n;
-    const int64_t nn = (int64_t)n * n;
-    const int64_t st = (mode == 0) ? nn : (int64_t)n;                 // stride of the solved mode
-    const int64_t st2 = 2 * st;
-    const int64_t o = ((mode == 0) ? (int64_t)other * n : (int64_t)other * nn) + k0 + lane + par * st;  // t = par
-    const int m = (n - par + 1) / 2;  // unknowns of this parity
-    T z = 0, u_prev = 0;
-    for (int i0 = 0; i0 < m; i0 += kU) {
-        T r[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            r[u] = 0;
-            if (act && i0 + u < m) {
-                const int64_t at = o + (int64_t)(i0 + u) * st2;
-                T v = s1 * R1[at];
-                if (R2) v = fma(s2, R2[at], v);
-                r[u] = v;
-            }
+    const int tsz = line_tile_elems(n, CONTIG);
+    F2 *fs = reinterpret_cast<F2 *>(smem_raw);  // the factor set, n entries
+    T *A = reinterpret_cast<T *>(fs + n);
+    T *B = A + tsz;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) fs[t] = fac[t];
+    const int pitch = CONTIG ? contig_pitch(n) : 0;
+    // geometry: element (li, t) of the tile <-> global offset gbase + li * gl + t * gt
+    int nl;
+    int64_t gbase, gl, gt;
+    if (CONTIG) {
+        const int L0 = blockIdx.x * kLines;
+        nl = min(kLines, n * n - L0);
+        gbase = (int64_t)L0 * n;
+        gl = n;
+        gt = 1;
+    } else {
+        const int nkb = (n + kLines - 1) / kLines;
+        const int other = blockIdx.x / nkb, k0 = (blockIdx.x % nkb) * kLines;
+        const int64_t nn = (int64_t)n * n;
+        nl = min(kLines, n - k0);
+        gbase = ((mode == 0) ? (int64_t)other * n : (int64_t)other * nn) + k0;
+        gl = 1;
+        gt = (mode == 0) ? nn : (int64_t)n;
+    }
+    auto sidx = [&](int li, int t) { return CONTIG ? li * pitch + t : t * kLines + li; };
+    // element q of the tile in load/store order (consecutive threads -> consecutive addresses)
+    auto qmap = [&](int q, int &li, int &t) {
+        if (CONTIG) {
+            li = q / n;
+            t = q - li * n;
+        } else {
+            t = q >> 5;
+            li = q & 31;
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int i = i0 + u;
-            if (i < m) {
-                z = fma(-u_prev, z, r[u]);
-                zs[i * kLines + lane] = z;
-                u_prev = fac[par + 2 * i].y;
-            }
+    };
+    const int total = kLines * n;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        int li, t;
+        qmap(q, li, t);
+        if (li < nl) {
+            const int64_t g = gbase + li * gl + t * gt;
+            cp_async_elem(&A[sidx(li, t)], R1 + g);
+            if (R2 && !preband) cp_async_elem(&B[sidx(li, t)], R2 + g);
         }
     }
-    __syncwarp();
-    T x = 0;
-    for (int i0 = m - 1; i0 >= 0; i0 -= kU) {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    // IN into B
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        int li, t;
+        qmap(q, li, t);
+        if (li < nl) {
+            const int k = sidx(li, t);
+            T v;
+            if (preband) {
+                v = d[t] * A[k];
+                if (t >= 2) v = fma(e[t - 2], A[sidx(li, t - 2)], v);
+                if (t + 2 < n) v = fma(e[t], A[sidx(li, t + 2)], v);
+                v *= s1;
+            } else {
+                v = s1 * A[k];
+                if (R2) v = fma(s2, B[k], v);
+            }
+            B[k] = v;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
+    const int m = (n - par + 1) / 2;  // unknowns of this parity: t = par + 2 i, i < m
+    if (lane < nl) {
+        // Both sweeps in chunks of kC steps: the chunk's operands are read from shared
+        // memory first, so only the kC dependent FMAs remain on the critical path.
+        constexpr int kC = 8;
+        T z = 0, u_prev = 0;
+        for (int i0 = 0; i0 < m; i0 += kC) {
+            T in[kC], uf[kC];
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int t = par + 2 * min(i0 + u, m - 1);
+                in[u] = B[sidx(lane, t)];
+                uf[u] = fs[t].y;
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (i0 + u < m) {
+                    z = fma(-u_prev, z, in[u]);
+                    A[sidx(lane, par + 2 * (i0 + u))] = z;
+                    u_prev = uf[u];
+                }
+        }
+        T x = 0;
+        for (int i0 = m - 1; i0 >= 0; i0 -= kC) {
+            T zz[kC];
+            F2 ff[kC];
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int t = par + 2 * max(i0 - u, 0);
+                zz[u] = A[sidx(lane, t)];
+                ff[u] = fs[t];
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (i0 - u >= 0) {
+                    x = fma(-ff[u].y, x, ff[u].x * zz[u]);
+                    A[sidx(lane, par + 2 * (i0 - u))] = x;
+                }
+        }
+    }
+    __syncthreads();
+    for (int q0 = threadIdx.x; q0 < total; q0 += kU * blockDim.x) {
         T xo[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
+            const int q = q0 + u * blockDim.x;
             xo[u] = 0;
-            if (oacc != T(0) && act && i0 - u >= 0) xo[u] = X[o + (int64_t)(i0 - u) * st2];
+            if (oacc != T(0) && q < total) {
+                int li, t;
+                qmap(q, li, t);
+                if (li < nl) xo[u] = X[gbase + li * gl + t * gt];
+            }
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int i = i0 - u;
-            if (i >= 0) {
-                const auto f = fac[par + 2 * i];
-                x = fma(-f.y, x, f.x * zs[i * kLines + lane]);
-                if (act) {
-                    const T v = oscale * x;
-                    X[o + (int64_t)i * st2] = (oacc != T(0)) ? fma(oacc, xo[u], v) : v;
+            const int q = q0 + u * blockDim.x;
+            if (q < total) {
+                int li, t;
+                qmap(q, li, t);
+                if (li < nl) {
+                    const int k = sidx(li, t);
+                    T v = oscale * A[k];
+                    if (oin != T(0)) v = fma(oin, B[k], v);
+                    if (oacc != T(0)) v = fma(oacc, xo[u], v);
+                    X[gbase + li * gl + t * gt] = v;
                 }
             }
         }
     }
-}
-
-// Shared-memory row pitch of the contiguous-mode tile: odd, so that the 32 lanes
-// of a warp (one line each, same t) hit distinct banks.
-__host__ __device__ __forceinline__ int contig_pitch(int n) { return (n % 2 == 0) ? n + 1 : n + 2; }
-
-// Same along mode 2 (contiguous lines): a CTA loads kLines consecutive lines into a
-// shared-memory tile (coalesced, kU rows in flight per thread), runs the sweeps of
-// each (line, parity) there (warp = parity, lane = line), and writes the tile back.
-template <typename T>
-__global__ void __launch_bounds__(64) cube_solve_contig_kernel(const typename V2<T>::type *__restrict__ fac,
-                                                               const T *R1, T s1, const T *R2, T s2, T *X, int n,
-                                                               T oscale, T oacc)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw);  // kLines x pitch
-    const int pitch = contig_pitch(n);
-    const int nlines = n * n;
-    const int L0 = blockIdx.x * kLines;
-    const int nl = min(kLines, nlines - L0);
-    const int64_t base = (int64_t)L0 * n;
-    for (int li0 = 0; li0 < nl; li0 += kU)
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            T r[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                r[u] = 0;
-                if (li0 + u < nl) {
-                    const int64_t at = base + (int64_t)(li0 + u) * n + t;
-                    T v = s1 * R1[at];
-                    if (R2) v = fma(s2, R2[at], v);
-                    r[u] = v;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (li0 + u < nl) tile[(li0 + u) * pitch + t] = r[u];
-        }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
-    if (lane < nl) {
-        T *row = tile + lane * pitch;
-        T z = 0, u_prev = 0;
-        for (int t = par; t < n; t += 2) {
-            z = fma(-u_prev, z, row[t]);
-            row[t] = z;
-            u_prev = fac[t].y;
-        }
-        T x = 0;
-        const int tlast = par + 2 * ((n - 1 - par) / 2);
-        for (int t = tlast; t >= 0; t -= 2) {
-            const auto f = fac[t];
-            x = fma(-f.y, x, f.x * row[t]);
-            row[t] = x;
-        }
-    }
-    __syncthreads();
-    for (int li0 = 0; li0 < nl; li0 += kU)
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            T xo[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                xo[u] = (oacc != T(0) && li0 + u < nl) ? X[base + (int64_t)(li0 + u) * n + t] : T(0);
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (li0 + u < nl) {
-                    const T v = oscale * tile[(li0 + u) * pitch + t];
-                    X[base + (int64_t)(li0 + u) * n + t] = (oacc != T(0)) ? fma(oacc, xo[u], v) : v;
-                }
-        }
 }
 
 // G = -F s_i s_j s_k (scale-in) or X = Y s_i s_j s_k (scale-out, sign = +1)
@@ -435,7 +480,7 @@ int CubeNested<T>::create(int64_t n, double tol, double tol_mid, double tol_in, 
     CUBE_CK(alloc((void **)&be64_, sizeof(double) * n));
     CUBE_CK(alloc((void **)&bd_, sizeof(T) * n));
     CUBE_CK(alloc((void **)&be_, sizeof(T) * n));
-    const int nwork = residual_ ? 11 : 8;
+    const int nwork = residual_ ? 9 : 8;
     for (int w = 0; w < nwork; ++w) CUBE_CK(alloc((void **)&work_[w], sizeof(T) * N));
     CUBE_CK(alloc(&fac_, sizeof(typename V2<T>::type) * (size_t)max_sets_ * n));
     CUBE_CK(alloc((void **)&ab_, sizeof(double2) * hab.size()));
@@ -444,10 +489,10 @@ int CubeNested<T>::create(int64_t n, double tol, double tol_mid, double tol_in, 
     CUBE_CK(cudaMemcpy(bd_, dT.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
     CUBE_CK(cudaMemcpy(be_, eT.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
     CUBE_CK(cudaMemcpy(ab_, hab.data(), sizeof(double2) * hab.size(), cudaMemcpyHostToDevice));
-    CUBE_CK(cudaFuncSetAttribute(cube_solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kLines * contig_pitch((int)n) * (int)sizeof(T)));
-    CUBE_CK(cudaFuncSetAttribute(cube_solve_strided_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * (int)((n + 1) / 2) * kLines * (int)sizeof(T)));
+    CUBE_CK(cudaFuncSetAttribute(cube_line_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 line_smem_bytes<T>((int)n, true)));
+    CUBE_CK(cudaFuncSetAttribute(cube_line_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 line_smem_bytes<T>((int)n, false)));
     fac_entry_ = -1;
     return FPS_OK;
 }
@@ -490,21 +535,22 @@ cudaError_t CubeNested<T>::axpy3(const T *X, const T *Y, const T *W, T *V, doubl
 
 template <typename T>
 cudaError_t CubeNested<T>::solve(int set, const T *R1, double s1, const T *R2, double s2, T *X, int mode,
-                                 double oscale, double oacc)
+                                 double oscale, double oacc, double oin, bool preband)
 {
     using F2 = typename V2<T>::type;
     const F2 *fac = reinterpret_cast<const F2 *>(fac_) + (int64_t)set * n_;
+    const int n = (int)n_;
     if (mode == 2) {
-        const int64_t nlines = n_ * n_;
-        const int blocks = (int)((nlines + kLines - 1) / kLines);
-        const int smem = kLines * contig_pitch((int)n_) * (int)sizeof(T);
-        cube_solve_contig_kernel<T><<<blocks, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, (int)n_,
-                                                                        (T)oscale, (T)oacc);
+        const int blocks = (n * n + kLines - 1) / kLines;
+        const int smem = line_smem_bytes<T>(n, true);
+        cube_line_kernel<T, true><<<blocks, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
+                                                                     (T)oscale, (T)oin, (T)oacc, preband, bd_, be_);
     } else {
-        const int nkb = (int)((n_ + kLines - 1) / kLines);
-        const int smem = 2 * (int)((n_ + 1) / 2) * kLines * (int)sizeof(T);
-        cube_solve_strided_kernel<T><<<(unsigned)(n_ * nkb), 2 * kLines, smem, st_>>>(
-            fac, R1, (T)s1, R2, (T)s2, X, (int)n_, mode, (T)oscale, (T)oacc);
+        const int nkb = (n + kLines - 1) / kLines;
+        const int smem = line_smem_bytes<T>(n, false);
+        cube_line_kernel<T, false><<<n * nkb, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
+                                                                       (T)oscale, (T)oin, (T)oacc, preband, bd_,
+                                                                       be_);
     }
     ++launches;
     return cudaGetLastError();
@@ -542,9 +588,9 @@ int CubeNested<T>::stein(int ma, int mb, int entry, const T *R, T *Z, std::strin
             CUBE_CK(band(W1, R, W2, ma, 1.0, -S.p[l], -1.0, 1.0));                // R - (A~_a - p) ( . )
             U = W2;
         }
-        CUBE_CK(solve(1 + 2 * l, U, 1.0, nullptr, 0.0, W1, mb, 1.0, 0.0));      // Z_h = ( . ) (c + p A~_b)^{-1}
-        CUBE_CK(solve(0, R, 1.0, W1, -c, W2, mb, 1.0, 0.0));                     // (R - c Z_h) A~_b^{-1}
-        CUBE_CK(solve(2 + 2 * l, W2, 1.0, W1, -S.q[l], Z, ma, 1.0, 0.0));        // (A~_a - q)^{-1} ( . - q Z_h)
+        CUBE_CK(solve(1 + 2 * l, U, 1.0, nullptr, 0.0, W1, mb, 1.0, 0.0, 0.0, false));  // Z_h = ( . ) (c + p A~_b)^{-1}
+        CUBE_CK(solve(0, R, 1.0, W1, -c, W2, mb, 1.0, 0.0, 0.0, false));                 // (R - c Z_h) A~_b^{-1}
+        CUBE_CK(solve(2 + 2 * l, W2, 1.0, W1, -S.q[l], Z, ma, 1.0, 0.0, 0.0, false));    // (A~_a - q)^{-1} ( . - q Z_h)
     }
     return FPS_OK;
 }
@@ -582,31 +628,27 @@ int CubeNested<T>::hsolve(const Outer &o, const T *R, T *Y, std::string &err)
 // rho = C - A Z + Z B the two half-steps of Algorithm 2 become
 //   rho+ = (A - q)^{-1} (A - p) rho (B - p)^{-1} (B - q),
 //   Z+   = Z + (q - p) (A - q)^{-1} rho (B - p)^{-1},
-// and rho (B - p)^{-1} = -rho A~_b (c + p A~_b)^{-1}.  Per iteration: one product and
-// one solve along b, two solves along a.  Uses work_[0..2].
+// and rho (B - p)^{-1} = -rho A~_b (c + p A~_b)^{-1}.  Per iteration three line-solve
+// launches: a1 = rho (B - p)^{-1} along b (the product with A~_b folded in), then
+// along a rho+ = c1 + (q - p)(A - q)^{-1} c1 with c1 = rho + (p - q) a1 (in place)
+// and Z += (q - p)(A - q)^{-1} a1.  Solves Z = (T_ab + c)^{-1} (r1 R1 + r2 R2), or
+// adds it to Z when accumulate.  Uses work_[0], work_[1].
 template <typename T>
-int CubeNested<T>::stein_res(int ma, int mb, int entry, const T *R, T *Z, std::string &err)
+int CubeNested<T>::stein_res(int ma, int mb, int entry, const T *R1, double r1, const T *R2, double r2, T *Z,
+                             bool accumulate, std::string &err)
 {
     int st = load_factors(entry, err);
     if (st != FPS_OK) return st;
     const Stein &S = steins_[entry];
-    T *rho = work_[0], *a1 = work_[1], *g = work_[2];
-    CUBE_CK(solve(0, R, 1.0, nullptr, 0.0, rho, mb, 1.0, 0.0));                 // rho = R A~_b^{-1}
+    T *rho = work_[0], *a1 = work_[1];
+    CUBE_CK(solve(0, R1, r1, R2, r2, rho, mb, 1.0, 0.0, 0.0, false));                  // rho = R A~_b^{-1}
     for (int l = 0; l < S.J; ++l) {
         const double p = S.p[l], q = S.q[l];
-        const T *t = R;                                                          // rho A~_b (= R at l = 0)
-        if (l > 0) {
-            CUBE_CK(band(rho, nullptr, a1, mb, 1.0, 0.0, 1.0, 0.0));
-            t = a1;
-        }
-        CUBE_CK(solve(1 + 2 * l, t, -1.0, nullptr, 0.0, a1, mb, 1.0, 0.0));     // a1 = rho (B - p)^{-1}
-        if (l + 1 < S.J) {
-            // rho+ = c1 + (q - p)(A - q)^{-1} c1 with c1 = rho + (p - q) a1
-            CUBE_CK(solve(2 + 2 * l, rho, 1.0, a1, p - q, g, ma, 1.0, 0.0));
-            CUBE_CK(axpy3(rho, a1, g, rho, 1.0, p - q, q - p));
-        }
-        // Z += (q - p)(A - q)^{-1} a1
-        CUBE_CK(solve(2 + 2 * l, a1, 1.0, nullptr, 0.0, Z, ma, q - p, l == 0 ? 0.0 : 1.0));
+        if (l == 0) CUBE_CK(solve(1, R1, -r1, R2, -r2, a1, mb, 1.0, 0.0, 0.0, false));    // rho A~_b = R
+        else CUBE_CK(solve(1 + 2 * l, rho, -1.0, nullptr, 0.0, a1, mb, 1.0, 0.0, 0.0, true));
+        if (l + 1 < S.J) CUBE_CK(solve(2 + 2 * l, rho, 1.0, a1, p - q, rho, ma, q - p, 0.0, 1.0, false));
+        CUBE_CK(solve(2 + 2 * l, a1, 1.0, nullptr, 0.0, Z, ma, q - p, (l > 0 || accumulate) ? 1.0 : 0.0, 0.0,
+                      false));
     }
     return FPS_OK;
 }
@@ -615,29 +657,25 @@ int CubeNested<T>::stein_res(int ma, int mb, int entry, const T *R, T *Z, std::s
 // B' = T_02 + s/2) and shifts +-a,
 //   rho+ = [I - 2a (A' + a)^{-1}] [I - 2a (B' + a)^{-1}] rho,
 //   W+   = W + (A' + a)^{-1} 2a (B' + a)^{-1} rho,
-// three slice Stein solves per iteration (two in the last).  Uses work_[3..6].
+// three slice Stein solves per iteration (two in the last).  Uses work_[3..5].
 template <typename T>
 int CubeNested<T>::hsolve_res(const Outer &o, const T *R, T *W, std::string &err)
 {
-    T *rho = work_[3], *v = work_[4], *c2 = work_[5], *g = work_[6];
+    T *rho = work_[3], *v = work_[4], *g = work_[5];
     const size_t J = o.mid.size();
     for (size_t m = 0; m < J; ++m) {
         const double a = o.mid[m].a;
         const int entry = o.mid[m].stein;
         const T *r = (m == 0) ? R : rho;
-        int st = stein_res(0, 2, entry, r, v, err);                          // v = (B' + a)^{-1} rho
+        int st = stein_res(0, 2, entry, r, 1.0, nullptr, 0.0, v, false, err);        // v = (B' + a)^{-1} rho
         if (st != FPS_OK) return st;
         if (m + 1 < J) {
-            CUBE_CK(axpby(r, v, c2, 1.0, -2.0 * a));                         // c2 = rho - 2a v
-            st = stein_res(0, 1, entry, c2, g, err);                         // g = (A' + a)^{-1} c2
+            st = stein_res(0, 1, entry, r, 1.0, v, -2.0 * a, g, false, err);         // g = (A' + a)^{-1} (rho - 2a v)
             if (st != FPS_OK) return st;
-            CUBE_CK(axpby(c2, g, rho, 1.0, -2.0 * a));                       // rho+ = c2 - 2a g
+            CUBE_CK(axpy3(r, v, g, rho, 1.0, -2.0 * a, -2.0 * a));                  // rho+ = rho - 2a v - 2a g
         }
-        CUBE_CK(axpby(v, v, c2, 2.0 * a, 0.0));                              // 2a v
-        st = stein_res(0, 1, entry, c2, g, err);                             // (A' + a)^{-1} 2a v
+        st = stein_res(0, 1, entry, v, 2.0 * a, nullptr, 0.0, W, m > 0, err);        // W += (A' + a)^{-1} 2a v
         if (st != FPS_OK) return st;
-        if (m == 0) CUBE_CK(axpby(g, g, W, 1.0, 0.0));
-        else CUBE_CK(axpby(W, g, W, 1.0, 1.0));
     }
     return FPS_OK;
 }
@@ -649,27 +687,23 @@ int CubeNested<T>::hsolve_res(const Outer &o, const T *R, T *W, std::string &err
 //   Y+   = Y + (V + p)^{-1} (p - q) (H - q)^{-1} rho:
 // only residuals are solved with and no product with H or V of a growing iterate
 // is formed, which keeps FP32 rounding relative to the residual (the paper's form
-// loses it to cancellation at small shifts).  Uses work_[7..10].
+// loses it to cancellation at small shifts).  Uses work_[6..8].
 template <typename T>
 int CubeNested<T>::run_residual(const T *G, T *Y, std::string &err)
 {
-    T *rho = work_[7], *w = work_[8], *cb = work_[9], *u = work_[10];
+    T *rho = work_[6], *w = work_[7], *u = work_[8];
     for (int j = 0; j < J_outer; ++j) {
         const Outer &o = outer_[j];
         const T *r = (j == 0) ? G : rho;
-        int s = hsolve_res(o, r, w, err);                               // w = (H - q)^{-1} rho
+        int s = hsolve_res(o, r, w, err);                                         // w = (H - q)^{-1} rho
         if (s != FPS_OK) return s;
-        CUBE_CK(axpby(r, w, cb, 1.0, o.q - o.p));                       // c = rho + (q - p) w
-        s = stein_res(1, 2, o.stein_v, cb, u, err);                     // u = (V + p)^{-1} c
-        if (s != FPS_OK) return s;
-        CUBE_CK(axpby(cb, u, rho, 1.0, o.q - o.p));                     // rho+ = c + (q - p) u
-        // the scalar p - q goes in before the solve: w ~ rho / eps^2 and
+        s = stein_res(1, 2, o.stein_v, r, 1.0, w, o.q - o.p, u, false, err);      // u = (V + p)^{-1} c,
+        if (s != FPS_OK) return s;                                                //   c = rho + (q - p) w
+        CUBE_CK(axpy3(r, w, u, rho, 1.0, o.q - o.p, o.q - o.p));                  // rho+ = c + (q - p) u
+        // the scalar p - q enters with the right-hand side: w ~ rho / eps^2 and
         // (V + p)^{-1} w ~ rho / eps^4 would leave the FP32 range for n >~ 100
-        CUBE_CK(axpby(w, w, cb, o.p - o.q, 0.0));
-        s = stein_res(1, 2, o.stein_v, cb, u, err);                     // b = (V + p)^{-1} (p - q) w
+        s = stein_res(1, 2, o.stein_v, w, o.p - o.q, nullptr, 0.0, Y, j > 0, err); // Y += (V + p)^{-1} (p - q) w
         if (s != FPS_OK) return s;
-        if (j == 0) CUBE_CK(axpby(u, u, Y, 1.0, 0.0));                  // Y = b
-        else CUBE_CK(axpby(Y, u, Y, 1.0, 1.0));                         // Y += b
     }
     return FPS_OK;
 }

@@ -50,13 +50,15 @@ private:
     cudaError_t band(const T *X, const T *R, T *Y, int mode, double alpha, double beta, double sop, double sr);
     cudaError_t axpby(const T *X, const T *Y, T *Z, double a, double b);
     cudaError_t axpy3(const T *X, const T *Y, const T *W, T *V, double a, double b, double c);
-    // X = oscale * (alpha A~ + beta)^{-1} (s1 R1 + s2 R2) + oacc * X along `mode`
+    // X = oscale * (alpha A~ + beta)^{-1} IN + oin * IN + oacc * X along `mode`, with
+    // IN = s1 R1 + s2 R2, or IN = s1 A~ R1 along `mode` when preband
     cudaError_t solve(int set, const T *R1, double s1, const T *R2, double s2, T *X, int mode, double oscale,
-                      double oacc);
+                      double oacc, double oin, bool preband);
     int load_factors(int entry, std::string &err);
     int stein(int ma, int mb, int entry, const T *R, T *Z, std::string &err);
     int hsolve(const Outer &o, const T *R, T *Y, std::string &err);
-    int stein_res(int ma, int mb, int entry, const T *R, T *Z, std::string &err);
+    int stein_res(int ma, int mb, int entry, const T *R1, double r1, const T *R2, double r2, T *Z, bool accumulate,
+                  std::string &err);
     int hsolve_res(const Outer &o, const T *R, T *W, std::string &err);
     int run_residual(const T *G, T *Y, std::string &err);
     int add_stein(double c);
@@ -67,7 +69,7 @@ private:
     cudaStream_t st_ = nullptr;
     double *bd64_ = nullptr, *be64_ = nullptr;
     T *bd_ = nullptr, *be_ = nullptr;
-    T *work_[11] = {nullptr};
+    T *work_[9] = {nullptr};
     void *fac_ = nullptr;        // factor sets of the current Stein entry ({1/den, u} in T)
     double2 *ab_ = nullptr;      // (alpha, beta) of every factor set of every Stein entry
     int fac_entry_ = -1;         // entry whose factors fac_ holds (stream order makes reuse safe)
