@@ -133,20 +133,30 @@ __host__ __device__ __forceinline__ int line_tile_elems(int n, bool contig)
     return contig ? kLines * contig_pitch(n) : kLines * n;
 }
 
-// Dynamic shared memory of the line solve: the factor set and two tiles.
+// Dynamic shared memory of the line solve: the factor set and one or two tiles.
 template <typename T>
-int line_smem_bytes(int n, bool contig)
+int line_smem_bytes(int n, bool contig, int ntiles)
 {
-    return n * (int)sizeof(typename V2<T>::type) + 2 * line_tile_elems(n, contig) * (int)sizeof(T);
+    return n * (int)sizeof(typename V2<T>::type) + ntiles * line_tile_elems(n, contig) * (int)sizeof(T);
+}
+
+// 16-byte asynchronous copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
 // Banded solves along one mode for kLines lines per CTA:
 //   IN = s1 R1 + s2 R2            (preband: IN = s1 (A~ R1) along the mode, R2 unused)
 //   X  = oscale (alpha A~ + beta)^{-1} IN + oin IN + oacc X      (X read only if oacc != 0)
-// The whole tile of R1 (and R2) is fetched with asynchronous copies, so one CTA has
-// all its bytes in flight at once; the input combination and both Thomas sweeps
-// (App. B parity decoupling: warp = parity, lane = line) run in shared memory, and
-// the output combination is written back coalesced.  X may alias R1 or R2.
+// The whole tile of R1 (and R2) is fetched with asynchronous copies (16-byte ones
+// when the rows are aligned), so one CTA has all its bytes in flight at once.  The
+// forward sweep forms IN as it goes; both Thomas sweeps (App. B parity decoupling:
+// warp = parity, lane = line) run in shared memory in chunks whose operands are
+// read ahead of the dependent FMAs, and the output combination is written back
+// coalesced.  X may alias R1 or R2.  Tile A holds R1, then z and x; tile B (present
+// when R2, oin or preband is used) holds R2, then IN (oin) or z and x (preband, A
+// keeping R1 for the stencil).
 // CONTIG (mode 2): kLines consecutive lines, tile [line][t].  Otherwise (modes 0,
 // 1): kLines lines adjacent in mode 2, one CTA per (index of the other strided mode,
 // block of kLines), tile [t][line].
@@ -193,39 +203,37 @@ __global__ void __launch_bounds__(64) cube_line_kernel(const typename V2<T>::typ
             li = q & 31;
         }
     };
+    const bool has_r2 = R2 != nullptr && !preband;
+    // strided tiles whose rows are whole, 16-byte aligned rows of the tensor move in
+    // 16-byte pieces (V elements)
+    constexpr int V = 16 / (int)sizeof(T);
+    const bool vec = !CONTIG && nl == kLines && ((gt * (int64_t)sizeof(T)) % 16 == 0) &&
+                     ((gbase * (int64_t)sizeof(T)) % 16 == 0) && (((uintptr_t)R1 & 15) == 0) &&
+                     (!has_r2 || ((uintptr_t)R2 & 15) == 0) && (((uintptr_t)X & 15) == 0) &&
+                     ((n * (int)sizeof(F2)) % 16 == 0);
     const int total = kLines * n;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        int li, t;
-        qmap(q, li, t);
-        if (li < nl) {
-            const int64_t g = gbase + li * gl + t * gt;
-            cp_async_elem(&A[sidx(li, t)], R1 + g);
-            if (R2 && !preband) cp_async_elem(&B[sidx(li, t)], R2 + g);
+    if (vec) {
+        for (int q = threadIdx.x * V; q < total; q += blockDim.x * V) {
+            const int t = q >> 5, li = q & 31;
+            const int64_t g = gbase + li + t * gt;
+            cp_async16(&A[t * kLines + li], R1 + g);
+            if (has_r2) cp_async16(&B[t * kLines + li], R2 + g);
+        }
+    } else {
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            int li, t;
+            qmap(q, li, t);
+            if (li < nl) {
+                const int64_t g = gbase + li * gl + t * gt;
+                cp_async_elem(&A[sidx(li, t)], R1 + g);
+                if (has_r2) cp_async_elem(&B[sidx(li, t)], R2 + g);
+            }
         }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // IN into B
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        int li, t;
-        qmap(q, li, t);
-        if (li < nl) {
-            const int k = sidx(li, t);
-            T v;
-            if (preband) {
-                v = d[t] * A[k];
-                if (t >= 2) v = fma(e[t - 2], A[sidx(li, t - 2)], v);
-                if (t + 2 < n) v = fma(e[t], A[sidx(li, t + 2)], v);
-                v *= s1;
-            } else {
-                v = s1 * A[k];
-                if (R2) v = fma(s2, B[k], v);
-            }
-            B[k] = v;
-        }
-    }
-    __syncthreads();
+    T *Z = preband ? B : A;  // z, then x
     const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
     const int m = (n - par + 1) / 2;  // unknowns of this parity: t = par + 2 i, i < m
     if (lane < nl) {
@@ -238,14 +246,26 @@ __global__ void __launch_bounds__(64) cube_line_kernel(const typename V2<T>::typ
 #pragma unroll
             for (int u = 0; u < kC; ++u) {
                 const int t = par + 2 * min(i0 + u, m - 1);
-                in[u] = B[sidx(lane, t)];
+                T v;
+                if (preband) {
+                    v = d[t] * A[sidx(lane, t)];
+                    if (t >= 2) v = fma(e[t - 2], A[sidx(lane, t - 2)], v);
+                    if (t + 2 < n) v = fma(e[t], A[sidx(lane, t + 2)], v);
+                    v *= s1;
+                } else {
+                    v = s1 * A[sidx(lane, t)];
+                    if (has_r2) v = fma(s2, B[sidx(lane, t)], v);
+                }
+                in[u] = v;
                 uf[u] = fs[t].y;
             }
 #pragma unroll
             for (int u = 0; u < kC; ++u)
                 if (i0 + u < m) {
+                    const int k = sidx(lane, par + 2 * (i0 + u));
                     z = fma(-u_prev, z, in[u]);
-                    A[sidx(lane, par + 2 * (i0 + u))] = z;
+                    Z[k] = z;
+                    if (oin != T(0)) B[k] = in[u];
                     u_prev = uf[u];
                 }
         }
@@ -256,42 +276,81 @@ __global__ void __launch_bounds__(64) cube_line_kernel(const typename V2<T>::typ
 #pragma unroll
             for (int u = 0; u < kC; ++u) {
                 const int t = par + 2 * max(i0 - u, 0);
-                zz[u] = A[sidx(lane, t)];
+                zz[u] = Z[sidx(lane, t)];
                 ff[u] = fs[t];
             }
 #pragma unroll
             for (int u = 0; u < kC; ++u)
                 if (i0 - u >= 0) {
                     x = fma(-ff[u].y, x, ff[u].x * zz[u]);
-                    A[sidx(lane, par + 2 * (i0 - u))] = x;
+                    Z[sidx(lane, par + 2 * (i0 - u))] = x;
                 }
         }
     }
     __syncthreads();
-    for (int q0 = threadIdx.x; q0 < total; q0 += kU * blockDim.x) {
-        T xo[kU];
+    if (vec) {
+        for (int q0 = threadIdx.x * V; q0 < total; q0 += kU * blockDim.x * V) {
+            T xo[kU][V];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int q = q0 + u * blockDim.x;
-            xo[u] = 0;
-            if (oacc != T(0) && q < total) {
-                int li, t;
-                qmap(q, li, t);
-                if (li < nl) xo[u] = X[gbase + li * gl + t * gt];
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + u * blockDim.x * V;
+#pragma unroll
+                for (int w = 0; w < V; ++w) xo[u][w] = 0;
+                if (oacc != T(0) && q < total) {
+                    const int t = q >> 5, li = q & 31;
+                    const T *src = X + gbase + li + t * gt;
+#pragma unroll
+                    for (int w = 0; w < V; ++w) xo[u][w] = src[w];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + u * blockDim.x * V;
+                if (q < total) {
+                    const int t = q >> 5, li = q & 31;
+                    const int k = t * kLines + li;
+                    T v[V];
+#pragma unroll
+                    for (int w = 0; w < V; ++w) {
+                        T val = oscale * Z[k + w];
+                        if (oin != T(0)) val = fma(oin, B[k + w], val);
+                        if (oacc != T(0)) val = fma(oacc, xo[u][w], val);
+                        v[w] = val;
+                    }
+                    T *dst = X + gbase + li + t * gt;
+                    if constexpr (sizeof(T) == 4)
+                        *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                    else
+                        *reinterpret_cast<double2 *>(dst) = make_double2(v[0], v[1]);
+                }
             }
         }
+    } else {
+        for (int q0 = threadIdx.x; q0 < total; q0 += kU * blockDim.x) {
+            T xo[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int q = q0 + u * blockDim.x;
-            if (q < total) {
-                int li, t;
-                qmap(q, li, t);
-                if (li < nl) {
-                    const int k = sidx(li, t);
-                    T v = oscale * A[k];
-                    if (oin != T(0)) v = fma(oin, B[k], v);
-                    if (oacc != T(0)) v = fma(oacc, xo[u], v);
-                    X[gbase + li * gl + t * gt] = v;
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + u * blockDim.x;
+                xo[u] = 0;
+                if (oacc != T(0) && q < total) {
+                    int li, t;
+                    qmap(q, li, t);
+                    if (li < nl) xo[u] = X[gbase + li * gl + t * gt];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + u * blockDim.x;
+                if (q < total) {
+                    int li, t;
+                    qmap(q, li, t);
+                    if (li < nl) {
+                        const int k = sidx(li, t);
+                        T v = oscale * Z[k];
+                        if (oin != T(0)) v = fma(oin, B[k], v);
+                        if (oacc != T(0)) v = fma(oacc, xo[u], v);
+                        X[gbase + li * gl + t * gt] = v;
+                    }
                 }
             }
         }
@@ -490,9 +549,9 @@ int CubeNested<T>::create(int64_t n, double tol, double tol_mid, double tol_in, 
     CUBE_CK(cudaMemcpy(be_, eT.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
     CUBE_CK(cudaMemcpy(ab_, hab.data(), sizeof(double2) * hab.size(), cudaMemcpyHostToDevice));
     CUBE_CK(cudaFuncSetAttribute(cube_line_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 line_smem_bytes<T>((int)n, true)));
+                                 line_smem_bytes<T>((int)n, true, 2)));
     CUBE_CK(cudaFuncSetAttribute(cube_line_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 line_smem_bytes<T>((int)n, false)));
+                                 line_smem_bytes<T>((int)n, false, 2)));
     fac_entry_ = -1;
     return FPS_OK;
 }
@@ -540,14 +599,15 @@ cudaError_t CubeNested<T>::solve(int set, const T *R1, double s1, const T *R2, d
     using F2 = typename V2<T>::type;
     const F2 *fac = reinterpret_cast<const F2 *>(fac_) + (int64_t)set * n_;
     const int n = (int)n_;
+    const int ntiles = (R2 != nullptr || oin != 0.0 || preband) ? 2 : 1;
     if (mode == 2) {
         const int blocks = (n * n + kLines - 1) / kLines;
-        const int smem = line_smem_bytes<T>(n, true);
+        const int smem = line_smem_bytes<T>(n, true, ntiles);
         cube_line_kernel<T, true><<<blocks, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
                                                                      (T)oscale, (T)oin, (T)oacc, preband, bd_, be_);
     } else {
         const int nkb = (n + kLines - 1) / kLines;
-        const int smem = line_smem_bytes<T>(n, false);
+        const int smem = line_smem_bytes<T>(n, false, ntiles);
         cube_line_kernel<T, false><<<n * nkb, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
                                                                        (T)oscale, (T)oin, (T)oacc, preband, bd_,
                                                                        be_);

@@ -43,8 +43,8 @@ namespace fps {
 namespace {
 
 constexpr int kRC = 32;        // columns per CTA
-constexpr int kChunk = 32;     // rows per checkpoint chunk (per parity)
-constexpr int kTileRows = 64;  // rows of a transposed-store tile (both parities)
+constexpr int kChunk = 16;     // rows per checkpoint chunk (per parity)
+constexpr int kTileRows = 2 * kChunk;  // rows of a transposed-store tile (both parities)
 constexpr int kU = 4;          // rows per shared-memory slot
 constexpr int kMaxSeg = 64;    // segments per (column, parity) system
 
@@ -224,8 +224,8 @@ __device__ __forceinline__ SlotMap make_slots(int tb, int te, int Ls, int m0)
     return sm;
 }
 
-// Transposed store of a 32 x 64 tile: Out[(k0 + cc) * ld + ibase + rr] for
-// cc < 32 (k0 + cc < n), rr < 64 (ibase + rr < ld), four rows per 16-byte store.
+// Transposed store of a 32 x kTileRows tile: Out[(k0 + cc) * ld + ibase + rr] for
+// cc < 32 (k0 + cc < n), rr < kTileRows (ibase + rr < ld), four rows per 16-byte store.
 // Rows beyond n inside the padded leading dimension receive don't-care values.
 __device__ __forceinline__ void store_tile(float *__restrict__ out, const float (*tile)[kTileRows + 1], int k0,
                                            int ibase, int n, int ld)

@@ -184,3 +184,15 @@ def test_cube_adjoint_gradient(api, precision, tol, ndir):
             worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * gnorm))
     api.plan_destroy(plan)
     assert worst <= 1e-6, worst
+
+
+@pytest.mark.slow
+def test_cube_refine_full_size(api):
+    """The n = 256 cube workload (F = g/((1+i)^2 (1+j)^2 (1+k)^2), seed 6), FP32 sweeps with
+    FP64 refinement to 1e-10, against the exact solution by diagonalisation of A~."""
+    n = 256
+    F = inputs.cube_rhs(n, 6)
+    X, info = _cube_plan_solve(api, F, "fp32_refine", 1e-10)
+    Xd = _cube_by_diagonalisation(F)
+    assert info["last_residual"] <= 1e-10
+    assert _relmax(X, Xd) <= 1e-10
