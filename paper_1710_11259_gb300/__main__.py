@@ -1,10 +1,12 @@
-"""Command line: plan and run square solves on synthetic right-hand sides.
+"""Command line: plan and run square or cube solves on synthetic right-hand sides.
 
     python -m paper_1710_11259_gb300 --n 4096 --precision fp32_refine --reps 3 [--seed 2] [--power 2]
+    python -m paper_1710_11259_gb300 --dim 3 --n 256 --seed 6 --reps 0 [--tol 0.5]
 
 Creates one plan, runs one warm-up solve and `reps` more solves on cuda:0 and
-prints the plan facts and the mean time per solve (CUDA events).  Used as the
-program under ncu when profiling a kernel on a chosen size.
+prints the plan facts and the mean time per timed solve (CUDA events).  Used as
+the program under ncu when profiling a kernel on a chosen size.  Square right-hand
+sides are F = g/((1+j)^p (1+k)^p), cube ones g/((1+i)^p (1+j)^p (1+k)^p).
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ import json
 def main() -> None:
     ap = argparse.ArgumentParser(prog="python -m paper_1710_11259_gb300")
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3])
     ap.add_argument("--precision", default="fp32_refine", choices=["fp64", "fp32_refine"])
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--reps", type=int, default=1)
@@ -28,20 +31,26 @@ def main() -> None:
 
     build_ext.build()
     tol = a.tol if a.tol is not None else (1e-13 if a.precision == "fp64" else 1e-10)
-    F = torch.from_numpy(inputs.square_rhs(a.n, a.seed, power=a.power)).cuda()
-    plan = api.plan_create(a.n, 2, tol, a.precision)
-    X = api.poisson_square_solve(plan, F)
+    if a.dim == 2:
+        F = torch.from_numpy(inputs.square_rhs(a.n, a.seed, power=a.power)).cuda()
+        solve = api.poisson_square_solve
+    else:
+        F = torch.from_numpy(inputs.cube_rhs(a.n, a.seed, power=a.power)).cuda()
+        solve = api.poisson_cube_solve
+    plan = api.plan_create(a.n, a.dim, tol, a.precision)
+    X = solve(plan, F)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.reps):
-        api.poisson_square_solve(plan, F, X)
+        solve(plan, F, X)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(a.reps, 1)
     info = api.plan_info(plan)
     api.plan_destroy(plan)
-    print(json.dumps({"n": a.n, "precision": a.precision, "tol": tol, "ms_per_solve": ms,
-                      "dofs_per_s": a.n * a.n / (ms * 1e-3) if ms > 0 else None, **info}))
+    print(json.dumps({"n": a.n, "dim": a.dim, "precision": a.precision, "tol": tol,
+                      "ms_per_solve": ms if a.reps > 0 else None,
+                      "dofs_per_s": a.n ** a.dim / (ms * 1e-3) if a.reps > 0 and ms > 0 else None, **info}))
 
 
 if __name__ == "__main__":
