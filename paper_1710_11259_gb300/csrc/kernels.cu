@@ -13,6 +13,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCols = 32;   // columns per CTA (one warp per row parity)
 constexpr int kTR = 32;     // rows per transposed-store tile
 constexpr int kRing = 16;   // prefetch depth (rows) of the per-warp rings
+constexpr int kGrp = 4;     // rows per ring wait: their independent work (stencil, scaling) overlaps
 
 template <typename T> struct Pair;
 template <> struct Pair<double> { using type = double2; };
@@ -114,23 +115,37 @@ __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, c
         }
         cp_commit();
     };
-    for (int t = 0; t < D - 1; ++t) issue_fwd(t);
+    // Rows are consumed kGrp at a time: the stencils of a group are independent, so
+    // only the recurrence z_i = r_i - uf z_{i-2} stays serial.  One commit group per
+    // row; D - kGrp rows stay in flight.
+    for (int t = 0; t < D - kGrp; ++t) issue_fwd(t);
     T z = 0, uf_prev = 0;
-    for (int64_t t = 0; t < m; ++t) {
+    for (int64_t t0 = 0; t0 < m; t0 += kGrp) {
         __syncwarp();
-        issue_fwd(t + D - 1);
-        cp_wait<D - 1>();
+#pragma unroll
+        for (int g = 0; g < kGrp; ++g) issue_fwd(t0 + D - kGrp + g);
+        cp_wait<D - kGrp>();
         __syncwarp();
-        const int s = (int)(t % D);
-        T r = R.fw.g[s][lane];
-        if (!ZERO_V) {
-            r = fma(-em, R.fw.v[s][lane], r);
-            r = fma(-c0, R.fw.v[s][lane + 2], r);
-            r = fma(-ep, R.fw.v[s][lane + 4], r);
+        T r[kGrp], ufs[kGrp];
+#pragma unroll
+        for (int g = 0; g < kGrp; ++g) {
+            const int s = (int)((t0 + g) % D);
+            T a = R.fw.g[s][lane];
+            if (!ZERO_V) {
+                a = fma(-em, R.fw.v[s][lane], a);
+                a = fma(-c0, R.fw.v[s][lane + 2], a);
+                a = fma(-ep, R.fw.v[s][lane + 4], a);
+            }
+            r[g] = a;
+            ufs[g] = R.fw.f[s].y;
         }
-        z = fma(-uf_prev, z, r);
-        uf_prev = R.fw.f[s].y;
-        if (kin) Z[(par + 2 * t) * n + k] = z;
+#pragma unroll
+        for (int g = 0; g < kGrp; ++g)
+            if (t0 + g < m) {
+                z = fma(-uf_prev, z, r[g]);
+                uf_prev = ufs[g];
+                if (kin) Z[(par + 2 * (t0 + g)) * n + k] = z;
+            }
     }
     cp_wait<0>();
     __syncwarp();
@@ -146,19 +161,32 @@ __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, c
         }
         cp_commit();
     };
-    for (int u = 0; u < D - 1; ++u) issue_bwd(u);
+    // Rows again kGrp at a time (each iteration issues as many rows as it consumes,
+    // so D - kGrp stay in flight); the products ip z of a group are independent.
+    for (int u = 0; u < D - kGrp; ++u) issue_bwd(u);
     T x = 0;
     int64_t u = 0;
     if (!TRANS) {
-        for (; u < m; ++u) {
+        for (; u < m; u += kGrp) {
             __syncwarp();
-            issue_bwd(u + D - 1);
-            cp_wait<D - 1>();
+#pragma unroll
+            for (int g = 0; g < kGrp; ++g) issue_bwd(u + D - kGrp + g);
+            cp_wait<D - kGrp>();
             __syncwarp();
-            const int s = (int)(u % D);
-            const P f = R.bw.f[s];
-            x = fma(-f.y, x, f.x * R.bw.z[s][lane]);
-            if (kin) Out[(par + 2 * (m - 1 - u)) * n + k] = x;
+            T w[kGrp], uf[kGrp];
+#pragma unroll
+            for (int g = 0; g < kGrp; ++g) {
+                const int s = (int)((u + g) % D);
+                const P f = R.bw.f[s];
+                w[g] = f.x * R.bw.z[s][lane];
+                uf[g] = f.y;
+            }
+#pragma unroll
+            for (int g = 0; g < kGrp; ++g)
+                if (u + g < m) {
+                    x = fma(-uf[g], x, w[g]);
+                    if (kin) Out[(par + 2 * (m - 1 - (u + g))) * n + k] = x;
+                }
         }
         cp_wait<0>();
         return;
@@ -169,15 +197,30 @@ __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, c
         const int64_t ihi = (ilo + kTR < n) ? ilo + kTR : n;
         int64_t istart = ihi - 1;
         if (((istart - par) & 1) != 0) --istart;
-        for (int64_t i = istart; i >= ilo; i -= 2, ++u) {
+        const int nr = (istart >= ilo) ? (int)((istart - ilo) / 2 + 1) : 0;  // rows of this parity in the tile
+        for (int r0 = 0; r0 < nr; r0 += kGrp) {
+            const int cnt = (nr - r0 < kGrp) ? nr - r0 : kGrp;
             __syncwarp();
-            issue_bwd(u + D - 1);
-            cp_wait<D - 1>();
+#pragma unroll
+            for (int g = 0; g < kGrp; ++g)
+                if (g < cnt) issue_bwd(u + D - kGrp + g);
+            cp_wait<D - kGrp>();
             __syncwarp();
-            const int s = (int)(u % D);
-            const P f = R.bw.f[s];
-            x = fma(-f.y, x, f.x * R.bw.z[s][lane]);
-            tile[lane][i - ilo] = x;
+            T w[kGrp], uf[kGrp];
+#pragma unroll
+            for (int g = 0; g < kGrp; ++g) {
+                const int s = (int)((u + g) % D);
+                const P f = R.bw.f[s];
+                w[g] = f.x * R.bw.z[s][lane];
+                uf[g] = f.y;
+            }
+#pragma unroll
+            for (int g = 0; g < kGrp; ++g)
+                if (g < cnt) {
+                    x = fma(-uf[g], x, w[g]);
+                    tile[lane][istart - 2 * (r0 + g) - ilo] = x;
+                }
+            u += cnt;
         }
         __syncthreads();
         const int rows = (int)(ihi - ilo);
