@@ -79,6 +79,8 @@ def _lib(variant: str = "double") -> ctypes.CDLL:
             lib.orc_poisson_cube.restype = ctypes.c_long
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+            lib.orc_legendre_to_ctilde.argtypes = [ctypes.c_long, c_dp, c_dp]
+            lib.orc_solution_to_legendre.argtypes = [ctypes.c_long, c_dp, c_dp]
             lib.orc_real_bytes.restype = ctypes.c_int
             _LIBS[variant] = lib
         return _LIBS[variant]
@@ -204,3 +206,24 @@ def real_bytes(variant: str = "double") -> int:
 if __name__ == "__main__":  # pragma: no cover
     build()
     print("oracle built in", _BUILD, file=sys.stderr)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.4 / Table 3.1 steps 1 and 4: Legendre coefficients in and out
+# --------------------------------------------------------------------------
+def legendre_to_ctilde(G) -> np.ndarray:
+    """F = B G B^T: C~ coefficients of sum G_ab P_a(y) P_b(x) (n x n)."""
+    G = _f64(G)
+    n = G.shape[0]
+    F = np.zeros_like(G)
+    _lib().orc_legendre_to_ctilde(n, _ptr(G), _ptr(F))
+    return F
+
+
+def solution_to_legendre(X) -> np.ndarray:
+    """Legendre coefficients ((n+2) x (n+2)) of u = (1-x^2)(1-y^2) sum X_ij C~_i(y) C~_j(x)."""
+    X = _f64(X)
+    n = X.shape[0]
+    U = np.zeros((n + 2, n + 2))
+    _lib().orc_solution_to_legendre(n, _ptr(X), _ptr(U))
+    return U

@@ -680,6 +680,96 @@ long orc_poisson_cube(long n, double tol, double tol_mid, double tol_in, const d
     return inner;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.4 / Table 3.1, steps 1 and 4: Legendre coefficients in and out.       */
+/* The conversion from Legendre to the C^(3/2) basis is banded:                 */
+/*   (2k+1) P_k = C^(3/2)_k - C^(3/2)_{k-2},                                    */
+/* so in the normalised basis C~_k = s_k C^(3/2)_k the C~ coefficients of       */
+/* sum_k g_k P_k are B g with B upper bidiagonal with stride 2.  On the way in  */
+/* F = B G B^T; on the way out the C~ coefficients of u = (1-x^2)(1-y^2) sum     */
+/* X_ij C~_i(y) C~_j(x) are W = M X M^T with M of (3.7) taken (n+2) x n, and    */
+/* the Legendre coefficients U solve B U B^T = W (back substitution).  This     */
+/* follows the reading that B maps Legendre to C~ (the direction is garbled in  */
+/* the printed text).                                                           */
+/* ------------------------------------------------------------------------- */
+
+/* s_k of C~_k = s_k C^(3/2)_k (footnote of Sec. 3.1) */
+static real ct_norm(long k)
+{
+    real K = (real)k;
+    return sqrt((K + (real)1.5) / ((K + 1) * (K + 2)));
+}
+
+/* P_k = C~_k / ((2k+1) s_k) - C~_{k-2} / ((2k+1) s_{k-2}):
+ * B[j][j] = 1/((2j+1) s_j), B[j][j+2] = -1/((2j+5) s_j). */
+static real B_diag(long j) { return 1 / ((2 * (real)j + 1) * ct_norm(j)); }
+static real B_off2(long j) { return -1 / ((2 * (real)j + 5) * ct_norm(j)); }
+
+/* F (n x n) = B G B^T for Legendre coefficients G[a*n + b] of sum G_ab P_a(y) P_b(x). */
+void orc_legendre_to_ctilde(long n, const double *G, double *F)
+{
+    real *T = malloc(sizeof(real) * (size_t)(n * n));
+    for (long j = 0; j < n; ++j) /* T = B G */
+        for (long k = 0; k < n; ++k) {
+            real v = B_diag(j) * (real)G[j * n + k];
+            if (j + 2 < n) v += B_off2(j) * (real)G[(j + 2) * n + k];
+            T[j * n + k] = v;
+        }
+    for (long j = 0; j < n; ++j) /* F = T B^T */
+        for (long k = 0; k < n; ++k) {
+            real v = B_diag(k) * T[j * n + k];
+            if (k + 2 < n) v += B_off2(k) * T[j * n + k + 2];
+            F[j * n + k] = (double)v;
+        }
+    free(T);
+}
+
+/* M[i][a] of (3.7) (symmetric, bands 0 and +-2), for any i, a >= 0 */
+static real M_entry(long i, long a)
+{
+    if (i == a) return M_diag(i);
+    if (i == a + 2) return M_off2(a);
+    if (a == i + 2) return M_off2(i);
+    return 0;
+}
+
+/* U ((n+2) x (n+2)): Legendre coefficients of u = (1-x^2)(1-y^2) sum X_ij C~_i(y) C~_j(x). */
+void orc_solution_to_legendre(long n, const double *X, double *U)
+{
+    long m = n + 2;
+    real *W1 = calloc((size_t)(m * n), sizeof(real));
+    real *W = calloc((size_t)(m * m), sizeof(real));
+    for (long i = 0; i < m; ++i) /* W1 = M X, (n+2) x n */
+        for (long k = 0; k < n; ++k) {
+            real v = 0;
+            for (long a = i - 2; a <= i + 2; a += 2)
+                if (a >= 0 && a < n) v += M_entry(i, a) * (real)X[a * n + k];
+            W1[i * n + k] = v;
+        }
+    for (long i = 0; i < m; ++i) /* W = W1 M^T, (n+2) x (n+2) */
+        for (long j = 0; j < m; ++j) {
+            real v = 0;
+            for (long b = j - 2; b <= j + 2; b += 2)
+                if (b >= 0 && b < n) v += W1[i * n + b] * M_entry(j, b);
+            W[i * m + j] = v;
+        }
+    for (long j = 0; j < m; ++j) /* B V = W, column by column from the bottom (V in W) */
+        for (long i = m - 1; i >= 0; --i) {
+            real v = W[i * m + j];
+            if (i + 2 < m) v -= B_off2(i) * W[(i + 2) * m + j];
+            W[i * m + j] = v / B_diag(i);
+        }
+    for (long i = 0; i < m; ++i) /* U B^T = V, row by row from the right */
+        for (long k = m - 1; k >= 0; --k) {
+            real v = W[i * m + k];
+            if (k + 2 < m) v -= B_off2(k) * W[i * m + k + 2];
+            W[i * m + k] = v / B_diag(k);
+        }
+    for (long t = 0; t < m * m; ++t) U[t] = (double)W[t];
+    free(W1);
+    free(W);
+}
+
 /* Threads OpenMP will use (reported beside the CPU-baseline timings). */
 int orc_num_threads(void)
 {

@@ -298,3 +298,52 @@ def test_cube_manufactured_polynomial():
     F, Xe = basis.manufactured_cube(pc, n)
     X, _, _ = oracle.poisson_cube(F, 1e-13)
     assert _relmax(X, Xe) < 5e-13
+
+
+# ------------------------------------------- Legendre in / Legendre out (Sec. 3.4)
+def _legendre_coeffs_2d(f, n, N):
+    """c_ab with f = sum c_ab P_a(y) P_b(x), by Gauss-Legendre quadrature (exact for
+    polynomials of degree < 2N - n in each variable)."""
+    x, w = np.polynomial.legendre.leggauss(N)
+    P = np.stack([np.polynomial.legendre.legval(x, np.eye(n)[a]) for a in range(n)])  # [a, node]
+    Xg, Yg = np.meshgrid(x, x, indexing="xy")  # Xg[iy, ix] = x[ix]
+    vals = f(Xg, Yg)
+    scale = (2 * np.arange(n) + 1) / 2.0
+    return (scale[:, None] * (P * w)) @ vals @ (scale[:, None] * (P * w)).T
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12])
+def test_legendre_to_ctilde_against_quadrature(n):
+    """F = B G B^T equals the C~ projection (Gauss-Jacobi quadrature) of sum G P_a(y) P_b(x)."""
+    G = inputs.gaussian(21, (n, n))
+    f = lambda X, Y: np.polynomial.legendre.legval2d(Y, X, G)
+    Fq = basis.project_2d(f, n, n + 4)
+    assert np.abs(oracle.legendre_to_ctilde(G) - Fq).max() <= 1e-13 * np.abs(Fq).max()
+
+
+@pytest.mark.parametrize("n", [1, 3, 10])
+def test_solution_to_legendre_pointwise(n):
+    """The Legendre series U reproduces u = (1-x^2)(1-y^2) sum X_ij C~_i(y) C~_j(x) at points."""
+    X = inputs.gaussian(22, (n, n))
+    U = oracle.solution_to_legendre(X)
+    pts = np.linspace(-0.97, 0.99, 9)
+    xs, ys = np.meshgrid(pts, pts)
+    Cx = basis.basis_matrix(n, xs.ravel())  # [j, point]
+    Cy = basis.basis_matrix(n, ys.ravel())
+    u = (1 - xs.ravel() ** 2) * (1 - ys.ravel() ** 2) * np.einsum("ip,ij,jp->p", Cy, X, Cx)
+    ul = np.polynomial.legendre.legval2d(ys.ravel(), xs.ravel(), U)
+    assert np.abs(u - ul).max() <= 1e-13 * np.abs(u).max()
+
+
+def test_legendre_roundtrip_manufactured():
+    """Legendre coefficients of f = Laplacian(u) in, solve (3.6), Legendre coefficients of
+    u = (1-x^2)(1-y^2) p out, against u's own coefficients (deg p <= 6, n = 16)."""
+    n = 16
+    pc = basis.monomial_coeffs(inputs.gaussian(23, (28,)), 6)
+    uc = basis.poly_times_bubble(pc)
+    fc = basis.laplacian(uc)
+    G = _legendre_coeffs_2d(lambda X, Y: basis.poly_eval(fc, X, Y), n, n + 8)
+    X = oracle.poisson_square(oracle.legendre_to_ctilde(G), 1e-13)
+    U = oracle.solution_to_legendre(X)
+    Ue = _legendre_coeffs_2d(lambda X, Y: basis.poly_eval(uc, X, Y), n + 2, n + 10)
+    assert np.abs(U - Ue).max() <= 1e-12 * np.abs(Ue).max()
