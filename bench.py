@@ -291,6 +291,23 @@ def main() -> None:
     info64 = api.plan_info(plan64)
     agree = float((X32 - X).abs().max().item() / X.abs().max().item())
 
+    # ---------------- Legendre coefficients in and out (banded 2D maps, HBM bound) ----------------
+    def event_ms(fn, reps=5):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    Fleg = torch.empty_like(F)
+    Uleg = torch.empty((N + 2, N + 2), dtype=torch.float64, device="cuda")
+    in_ms = event_ms(lambda: api.legendre_to_ctilde(F, Fleg, stream=stream.cuda_stream))
+    out_ms = event_ms(lambda: api.solution_to_legendre(X, Uleg, stream=stream.cuda_stream))
+    del Fleg, Uleg
+
     # ---------------- end to end: host buffers through the C ABI ----------------
     Fpin = torch.from_numpy(Fh).pin_memory()
     Xpin = torch.empty_like(Fpin).pin_memory()
@@ -348,6 +365,15 @@ def main() -> None:
         },
         "e2e": {"value": dofs_job / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 8 * N * N,
                 "d2h_bytes_per_step": 8 * N * N},
+        "legendre": {
+            "in_ms": in_ms, "out_ms": out_ms,
+            "in_gbs": 16.0 * N * N / (in_ms * 1e-3) / 1e9,
+            "out_gbs": (8.0 * N * N + 8.0 * (N + 2) ** 2) / (out_ms * 1e-3) / 1e9,
+            "in_frac": 16.0 * N * N / (in_ms * 1e-3) / 1e9 / hbm,
+            "out_frac": (8.0 * N * N + 8.0 * (N + 2) ** 2) / (out_ms * 1e-3) / 1e9 / hbm,
+            "note": "fps_legendre_to_ctilde / fps_solution_to_legendre at n=10^4 on device buffers; "
+                    "algorithmic bytes = one FP64 read and one FP64 write per element; outside the timed solve",
+        },
         "gpu_launches": int(info["kernel_launches"]) * args.steps,
         "clocks": clocks,
         "paper_context_dofs": PAPER_DOFS,

@@ -175,6 +175,29 @@ int fps_plan_set_instrument(fps_plan *plan, int on);
 int fps_plan_kernel_times(fps_plan *plan, int *count, double *total_ms, double *alg_bytes);
 
 /*
+ * fps_legendre_to_ctilde -- Legendre coefficients in (Sec. 3.4, Table 3.1 step 1):
+ * F = C~^(3/2) coefficients of f = sum_{a,b < n} G[a*n + b] P_a(y) P_b(x), as used by
+ * fps_poisson_square_solve.  With (2k+1) P_k = C^(3/2)_k - C^(3/2)_{k-2} the map is
+ * banded: F = B G B^T, B[j][j] = 1/((2j+1) s_j), B[j][j+2] = -1/((2j+5) s_j),
+ * C~_k = s_k C^(3/2)_k.  G and F: device pointers, n x n row-major, caller-owned,
+ * not overlapping; asynchronous on `stream`.  Errors: INVALID_ARG (n < 1, NULL,
+ * overlap, host memory), CUDA.
+ */
+int fps_legendre_to_ctilde(int64_t n, const double *G, double *F, void *stream);
+
+/*
+ * fps_solution_to_legendre -- Legendre coefficients out (Sec. 3.4, Table 3.1 step 4):
+ * U[i*(n+2) + k], i, k < n + 2, are the Legendre coefficients of the solution
+ * u = (1-x^2)(1-y^2) sum_{i,j < n} X[i*n + j] C~_i(y) C~_j(x) of (3.1)-(3.2), i.e.
+ * U = B^{-1} (M X M^T) B^{-T} with M of (3.7), computed as U = L X L^T with
+ * L[j][j] = c_j, L[j+2][j] = -c_j, c_j = s_j (j+1)(j+2)/(2j+3).  X (n x n) and U
+ * ((n+2) x (n+2)): device pointers, row-major, caller-owned, not overlapping;
+ * asynchronous on `stream`.  Errors: INVALID_ARG (n < 1, NULL, overlap, host
+ * memory), CUDA.
+ */
+int fps_solution_to_legendre(int64_t n, const double *X, double *U, void *stream);
+
+/*
  * fps_poisson_square_solve_noalloc -- the FP64 square solve of fps_poisson_square_solve
  * (same shifts, iteration count and kernels) for n <= 256, without allocating
  * anything.  The paper has no counterpart: this entry point exists for callers that

@@ -66,7 +66,7 @@ EXPORTED = [
     "fps_poisson_cube_solve", "fps_poisson_adjoint", "fps_plan_info", "fps_plan_shifts", "fps_plan_destroy",
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
     "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
-    "fps_square_spectral_interval",
+    "fps_square_spectral_interval", "fps_legendre_to_ctilde", "fps_solution_to_legendre",
 ]
 
 
@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.fps_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
         L.fps_poisson_square_solve_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp]
         L.fps_square_spectral_interval.argtypes = [i64, ctypes.c_int, dp, dp]
+        L.fps_legendre_to_ctilde.argtypes = [i64, vp, vp, vp]
+        L.fps_solution_to_legendre.argtypes = [i64, vp, vp, vp]
         _lib = L
         return L
 
@@ -260,6 +262,28 @@ def plan_destroy(plan: Plan) -> None:
     if plan._h:
         lib().fps_plan_destroy(plan._h)
         plan._h = ctypes.c_void_p()
+
+
+def legendre_to_ctilde(G, F=None, stream: Optional[int] = None):
+    """C~ coefficients F (n x n) of sum G_ab P_a(y) P_b(x); CUDA float64 tensors."""
+    import torch
+
+    n = int(G.shape[-1])
+    F = torch.empty_like(G) if F is None else F
+    s = _current_stream() if stream is None else int(stream)
+    _check(lib().fps_legendre_to_ctilde(n, ctypes.c_void_p(_ptr(G)), ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(s)))
+    return F
+
+
+def solution_to_legendre(X, U=None, stream: Optional[int] = None):
+    """Legendre coefficients U ((n+2) x (n+2)) of u = (1-x^2)(1-y^2) sum X_ij C~_i(y) C~_j(x)."""
+    import torch
+
+    n = int(X.shape[-1])
+    U = torch.empty((n + 2, n + 2), dtype=X.dtype, device=X.device) if U is None else U
+    s = _current_stream() if stream is None else int(stream)
+    _check(lib().fps_solution_to_legendre(n, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(U)), ctypes.c_void_p(s)))
+    return U
 
 
 def poisson_square_solve_noalloc(F, X, tol: float = 1e-13, stream: Optional[int] = None) -> int:

@@ -12,6 +12,7 @@
 #include "kernels.cuh"
 #include "refine_engine.h"
 #include "cube.h"
+#include "legendre.cuh"
 
 namespace {
 
@@ -626,5 +627,32 @@ int fps_square_spectral_interval(int64_t n, int tight, double *lo, double *hi)
 }
 
 int fps_build_arch(void) { return 103; }
+
+int fps_legendre_to_ctilde(int64_t n, const double *G, double *F, void *stream)
+{
+    if (n < 1) return fail(FPS_ERR_INVALID_ARG, "fps_legendre_to_ctilde: n must be >= 1");
+    if (!G || !F) return fail(FPS_ERR_INVALID_ARG, "fps_legendre_to_ctilde: NULL G or F");
+    const size_t bytes = sizeof(double) * (size_t)n * (size_t)n;
+    const char *g0 = (const char *)G, *f0 = (const char *)F;
+    if (g0 < f0 + bytes && f0 < g0 + bytes) return fail(FPS_ERR_INVALID_ARG, "fps_legendre_to_ctilde: G and F overlap");
+    if (!is_device_pointer(G) || !is_device_pointer(F))
+        return fail(FPS_ERR_INVALID_ARG, "fps_legendre_to_ctilde: G and F must be device memory");
+    FPS_CK(fps::launch_legendre_to_ctilde(G, F, n, (cudaStream_t)stream));
+    return FPS_OK;
+}
+
+int fps_solution_to_legendre(int64_t n, const double *X, double *U, void *stream)
+{
+    if (n < 1) return fail(FPS_ERR_INVALID_ARG, "fps_solution_to_legendre: n must be >= 1");
+    if (!X || !U) return fail(FPS_ERR_INVALID_ARG, "fps_solution_to_legendre: NULL X or U");
+    const size_t xb = sizeof(double) * (size_t)n * (size_t)n;
+    const size_t ub = sizeof(double) * (size_t)(n + 2) * (size_t)(n + 2);
+    const char *x0 = (const char *)X, *u0 = (const char *)U;
+    if (x0 < u0 + ub && u0 < x0 + xb) return fail(FPS_ERR_INVALID_ARG, "fps_solution_to_legendre: X and U overlap");
+    if (!is_device_pointer(X) || !is_device_pointer(U))
+        return fail(FPS_ERR_INVALID_ARG, "fps_solution_to_legendre: X and U must be device memory");
+    FPS_CK(fps::launch_solution_to_legendre(X, U, n, (cudaStream_t)stream));
+    return FPS_OK;
+}
 
 }  // extern "C"
