@@ -347,3 +347,23 @@ def test_legendre_roundtrip_manufactured():
     U = oracle.solution_to_legendre(X)
     Ue = _legendre_coeffs_2d(lambda X, Y: basis.poly_eval(uc, X, Y), n + 2, n + 10)
     assert np.abs(U - Ue).max() <= 1e-12 * np.abs(Ue).max()
+
+
+def test_cube_spectral_convergence_fig51():
+    """The cube discretisation converges spectrally to the true solution: for the
+    function of Fig. 5.1, u = (1-x^2)(1-y^2)(1-z^2) cos(x y z^2), the computed
+    coefficients approach the C~ coefficients of cos(x y z^2) (the ansatz (3.2) in
+    three variables) by orders of magnitude as n grows."""
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z")
+    u = (1 - x**2) * (1 - y**2) * (1 - z**2) * sp.cos(x * y * z**2)
+    f = sp.lambdify((x, y, z), sp.diff(u, x, 2) + sp.diff(u, y, 2) + sp.diff(u, z, 2), "numpy")
+    p = sp.lambdify((x, y, z), sp.cos(x * y * z**2), "numpy")
+    errs = []
+    for n in (4, 8, 12):
+        F = basis.project_3d(f, n, n + 24)
+        Xe = basis.project_3d(p, n, n + 24)
+        X, _, _ = oracle.poisson_cube(F, 1e-11, 1e-13, 1e-13)
+        errs.append(np.abs(X - Xe).max())
+    assert errs[0] > 1e2 * errs[1] > 1e4 * errs[2]
+    assert errs[2] < 1e-8
