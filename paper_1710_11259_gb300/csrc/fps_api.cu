@@ -345,7 +345,7 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     PCK(cudaMemcpyAsync(p->d_s, s.data(), sizeof(double) * n, cudaMemcpyHostToDevice, p->cap_stream));
     PCK(cudaMemcpyAsync(p->d_q, p->q.data(), sizeof(double) * p->J, cudaMemcpyHostToDevice, p->cap_stream));
     if (precision == FPS_FP64) {
-        PCK(fps::launch_factors(p->d_d, p->d_e, p->d_q, p->J, n, p->d_fac, nullptr, p->cap_stream));
+        PCK(fps::launch_factors(p->d_d, p->d_e, p->d_q, p->J, n, p->d_fac, p->cap_stream));
         PCK(cudaStreamSynchronize(p->cap_stream));
         int st = build_graph(p);
         if (st != FPS_OK) return bail(st);

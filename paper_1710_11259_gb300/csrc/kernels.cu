@@ -9,7 +9,6 @@ namespace fps {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCols = 32;   // columns per CTA (one warp per row parity)
 constexpr int kTR = 32;     // rows per transposed-store tile
 constexpr int kRing = 16;   // prefetch depth (rows) of the per-warp rings
@@ -235,7 +234,7 @@ __global__ void __launch_bounds__(64) halfstep_kernel(const T *__restrict__ V, c
 
 // Thomas factors of A~ - q_j I for one (shift, parity) per thread.
 __global__ void factor_kernel(const double *__restrict__ d, const double *__restrict__ e, const double *__restrict__ q,
-                              int J, int64_t n, double2 *__restrict__ fac, float2 *__restrict__ fac32)
+                              int J, int64_t n, double2 *__restrict__ fac)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= 2 * J) return;
@@ -248,7 +247,6 @@ __global__ void factor_kernel(const double *__restrict__ d, const double *__rest
         const double ip = 1.0 / den;
         const double uf = e[i] * ip;
         fac[(int64_t)j * n + i] = make_double2(ip, uf);
-        if (fac32) fac32[(int64_t)j * n + i] = make_float2((float)ip, (float)uf);
         uf_prev = uf;
     }
 }
@@ -307,13 +305,12 @@ cudaError_t launch_halfstep(const HalfStep<T> &h, cudaStream_t st)
 }
 
 template cudaError_t launch_halfstep<double>(const HalfStep<double> &, cudaStream_t);
-template cudaError_t launch_halfstep<float>(const HalfStep<float> &, cudaStream_t);
 
 cudaError_t launch_factors(const double *d, const double *e, const double *q, int J, int64_t n, double2 *fac,
-                           float2 *fac32, cudaStream_t st)
+                           cudaStream_t st)
 {
     const int threads = 2 * J;
-    factor_kernel<<<(threads + 127) / 128, 128, 0, st>>>(d, e, q, J, n, fac, fac32);
+    factor_kernel<<<(threads + 127) / 128, 128, 0, st>>>(d, e, q, J, n, fac);
     return cudaGetLastError();
 }
 

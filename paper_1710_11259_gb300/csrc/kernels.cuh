@@ -32,7 +32,7 @@ cudaError_t launch_halfstep(const HalfStep<T> &h, cudaStream_t st);
 // Per-shift Thomas factors of A~ - q_j I (FP64), J shifts, written as
 // fac[j*n + i] = {1/den_i, e_i/den_i}.  Optionally also an FP32 copy.
 cudaError_t launch_factors(const double *d, const double *e, const double *q, int J, int64_t n, double2 *fac,
-                           float2 *fac32, cudaStream_t st);
+                           cudaStream_t st);
 
 // F~ = D_s F D_s and its transpose (D_s = diag(s)).
 cudaError_t launch_scale_in(const double *F, double *Ft, double *FtT, const double *s, int64_t n, cudaStream_t st);

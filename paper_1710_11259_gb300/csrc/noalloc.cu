@@ -127,7 +127,7 @@ int fps_poisson_square_solve_noalloc(int64_t n, double tol, const double *F, dou
     NA_CK(cudaMemcpyAsync(d_e, e, sizeof(double) * n, cudaMemcpyHostToDevice, strm));
     NA_CK(cudaMemcpyAsync(d_s, s, sizeof(double) * n, cudaMemcpyHostToDevice, strm));
     NA_CK(cudaMemcpyAsync(d_q, q, sizeof(double) * J, cudaMemcpyHostToDevice, strm));
-    NA_CK(fps::launch_factors(d_d, d_e, d_q, J, n, fac, nullptr, strm));
+    NA_CK(fps::launch_factors(d_d, d_e, d_q, J, n, fac, strm));
     NA_CK(fps::launch_scale_in(F, Ft, FtT, d_s, n, strm));
     for (int j = 0; j < J; ++j) {
         fps::HalfStep<double> h;
