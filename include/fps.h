@@ -50,7 +50,7 @@ typedef enum {
 typedef enum {
     FPS_OK = 0,
     FPS_ERR_INVALID_ARG = -1,   /* bad size, tolerance, dimension, pointer */
-    FPS_ERR_UNSUPPORTED = -2,   /* valid request this build does not implement */
+    FPS_ERR_UNSUPPORTED = -2,   /* valid request the library does not implement */
     FPS_ERR_CUDA = -3,          /* a CUDA runtime call or launch failed */
     FPS_ERR_NOT_CONVERGED = -4, /* refinement missed its target; X holds the best iterate */
     FPS_ERR_NONFINITE = -5,     /* F (or an intermediate) holds NaN/Inf */

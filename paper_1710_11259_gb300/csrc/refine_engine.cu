@@ -11,7 +11,7 @@
 // what the worst active pair is missing; the first round uses the finest level
 // (1e-7, the accuracy an FP32 inner solve can deliver).  The inner shifts come from
 // a tight spectral interval of A~ (Sturm bisection) rather than Lemma B.2's: the
-// refinement is judged by the FP64 residual, not by matching a particular iterate.
+// refinement is assessed by the FP64 residual, not by matching a particular iterate.
 #include "refine_engine.h"
 
 #include <algorithm>
