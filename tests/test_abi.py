@@ -134,3 +134,18 @@ def test_tight_spectral_interval_contains_spectrum(L, n):
     assert lo <= -lam.max() and hi >= -lam.min()
     assert lo >= glo and hi <= ghi
     assert glo == 1.0 / (30.0 * n**4) and ghi == 1.0
+
+
+def test_legendre_conversion_argument_errors(L):
+    """Argument checks of the Legendre conversions run before any CUDA call."""
+    import ctypes
+
+    buf = (ctypes.c_double * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.fps_legendre_to_ctilde(0, p, p, None) == -1           # n < 1
+    assert L.fps_legendre_to_ctilde(4, None, p, None) == -1        # NULL
+    assert L.fps_legendre_to_ctilde(4, p, p, None) == -1           # overlap
+    assert L.fps_solution_to_legendre(0, p, p, None) == -1
+    assert L.fps_solution_to_legendre(2, p, None, None) == -1
+    assert L.fps_solution_to_legendre(2, p, p, None) == -1         # X inside U
+    assert b"overlap" in L.fps_last_error()
