@@ -34,6 +34,7 @@
 #include "../../include/fps.h"
 #include "cube.h"
 #include "host_math.h"
+#include "trace.h"
 
 namespace fps {
 
@@ -888,6 +889,7 @@ int CubeEngine::solve_cube(const double *F, double *X, cudaStream_t st, std::str
         double gmax = 0.0;
         int status = FPS_ERR_NOT_CONVERGED;
         for (int r = 0; r <= max_rounds; ++r) {
+            TraceRange tr("fps cube refinement round");
             CUBE_CK(cudaMemsetAsync(d_max_, 0, sizeof(unsigned long long), st));
             cube_residual_kernel<<<grid_for(N), 256, 0, st>>>(G_, Y_, bd_, be_, (int)n_, R_, r == 0, d_max_);
             ++launches_last;

@@ -13,6 +13,7 @@
 #include "refine_engine.h"
 #include "cube.h"
 #include "legendre.cuh"
+#include "trace.h"
 
 namespace {
 
@@ -222,6 +223,7 @@ int solve_engine(fps_plan *p, const double *F, double *X, bool fdev, bool xdev, 
 
 int solve_square(fps_plan *p, const double *F, double *X, const char *what)
 {
+    fps::TraceRange tr(what);
     if (!p) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": plan is NULL");
     if (p->dim != 2) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": plan is not two-dimensional");
     if (!F || !X) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": NULL F or X");
@@ -260,6 +262,7 @@ extern "C" {
 
 int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precision, int nrhs, void *stream)
 {
+    fps::TraceRange tr("fps_plan_create");
     if (!out) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: out is NULL");
     *out = nullptr;
     if (n < 1) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: n must be >= 1");
@@ -367,6 +370,7 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
 int fps_plan_create_batched(fps_plan **out, const int64_t *ns, int64_t count, int nrhs, double tol, int precision,
                             void *stream)
 {
+    fps::TraceRange tr("fps_plan_create_batched");
     if (!out) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_batched: out is NULL");
     *out = nullptr;
     if (!ns || count < 1) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_batched: need count >= 1 sizes");
@@ -424,6 +428,7 @@ int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X)
 
 int fps_poisson_cube_solve(fps_plan *plan, const double *F, double *X)
 {
+    fps::TraceRange tr("fps_poisson_cube_solve");
     if (!plan) return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: plan is NULL");
     if (plan->dim != 3 || !plan->cube)
         return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: plan is not three-dimensional");

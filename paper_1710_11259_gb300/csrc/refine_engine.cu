@@ -13,6 +13,7 @@
 // a tight spectral interval of A~ (Sturm bisection) rather than Lemma B.2's: the
 // refinement is assessed by the FP64 residual, not by matching a particular iterate.
 #include "refine_engine.h"
+#include "trace.h"
 
 #include <algorithm>
 #include <cmath>
@@ -596,6 +597,7 @@ int RefineEngine::solve(const double *F, double *X, cudaStream_t st, std::string
     int round = 0;
     bool converged = !any_active;
     for (; round < max_rounds && !converged; ++round) {
+        TraceRange tr("fps refinement round");
         double worst = 0.0;
         for (int k = 0; k < npairs_; ++k)
             if (h_pair_active_[k]) worst = std::max(worst, rel[k]);
