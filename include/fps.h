@@ -214,8 +214,11 @@ int fps_solution_to_legendre(int64_t n, const double *X, double *U, void *stream
  * make that first call before any stream capture.  All calls on a device share the
  * array, which keeps the last call's contents (each call rewrites everything it
  * reads); calls that overlap on the GPU race on it, so order them on one stream.
- * Errors (status code only; fps_last_error is not updated): INVALID_ARG (n or tol
- * out of range, NULL/overlapping/non-device F or X), CUDA.
+ * Nothing is copied from host memory (the bands of A~ are computed on the device,
+ * the shifts travel as a kernel argument).
+ * Errors: INVALID_ARG (n or tol out of range, NULL/overlapping F or X, F or X not
+ * device memory of the current device), CUDA.  fps_last_error() then returns a
+ * fixed message (a string literal: reporting the error allocates nothing).
  */
 int fps_poisson_square_solve_noalloc(int64_t n, double tol, const double *F, double *X, void *stream);
 

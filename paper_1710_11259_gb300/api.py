@@ -214,20 +214,39 @@ def _out_like(F, X):
     return torch.empty_like(F)
 
 
+def _numel(x) -> int:
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
+def _check_plan_buffers(plan: Plan, F, X) -> None:
+    """F must have the plan's shape (or be the packed 1-D array of that many
+    elements) and X as many elements: the library reads and writes exactly that."""
+    want = tuple(plan.shape())
+    count = int(np.prod(want))
+    shape = tuple(F.shape)
+    if not (shape == want or (len(shape) == 1 and shape[0] == count)):
+        raise FpsError(-1, f"input has shape {shape}; the plan expects {want}")
+    if _numel(X) != count:
+        raise FpsError(-1, f"output has {_numel(X)} elements; the plan writes {count}")
+
+
 def poisson_square_solve(plan: Plan, F, X=None):
     X = _out_like(F, X)
+    _check_plan_buffers(plan, F, X)
     _check(lib().fps_poisson_square_solve(plan.handle, ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(_ptr(X))))
     return X
 
 
 def poisson_cube_solve(plan: Plan, F, X=None):
     X = _out_like(F, X)
+    _check_plan_buffers(plan, F, X)
     _check(lib().fps_poisson_cube_solve(plan.handle, ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(_ptr(X))))
     return X
 
 
 def poisson_adjoint(plan: Plan, dLdX, dLdF=None):
     dLdF = _out_like(dLdX, dLdF)
+    _check_plan_buffers(plan, dLdX, dLdF)
     _check(lib().fps_poisson_adjoint(plan.handle, ctypes.c_void_p(_ptr(dLdX)), ctypes.c_void_p(_ptr(dLdF))))
     return dLdF
 
@@ -288,7 +307,12 @@ def solution_to_legendre(X, U=None, stream: Optional[int] = None):
 
 def poisson_square_solve_noalloc(F, X, tol: float = 1e-13, stream: Optional[int] = None) -> int:
     """FP64 square solve for n <= 256 that allocates nothing (see fps.h); F and X are
-    caller-allocated CUDA tensors.  Returns the status code (0 = ok)."""
+    caller-allocated n x n CUDA tensors on one device.  Returns the status code (0 = ok);
+    a malformed shape raises before the library is called."""
+    if len(F.shape) != 2 or F.shape[0] != F.shape[1] or tuple(X.shape) != tuple(F.shape):
+        raise FpsError(-1, f"F and X must both be n x n (got {tuple(F.shape)} and {tuple(X.shape)})")
+    if getattr(F, "device", None) != getattr(X, "device", None):
+        raise FpsError(-1, "F and X must be on the same device")
     s = _current_stream() if stream is None else int(stream)
     return int(lib().fps_poisson_square_solve_noalloc(int(F.shape[-1]), float(tol), ctypes.c_void_p(_ptr(F)),
                                                       ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(s)))

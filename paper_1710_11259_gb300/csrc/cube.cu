@@ -33,6 +33,7 @@
 
 #include "../../include/fps.h"
 #include "cube.h"
+#include "device_info.h"
 #include "host_math.h"
 #include "trace.h"
 
@@ -451,7 +452,7 @@ __global__ void cube_update_kernel(double *__restrict__ Y, const float *__restri
         Y[idx] = fma(sc, (double)delta[idx], first ? 0.0 : Y[idx]);
 }
 
-int grid_for(int64_t N) { return (int)std::min<int64_t>((N + 255) / 256, 152 * 16); }
+int grid_for(int64_t N) { return (int)std::min<int64_t>((N + 255) / 256, 16 * (int64_t)current_sm_count()); }
 
 }  // namespace
 

@@ -14,14 +14,17 @@
 #include "cube.h"
 #include "legendre.cuh"
 #include "trace.h"
+#include "status.h"
 
 namespace {
 
 thread_local std::string g_last_error;
+thread_local const char *g_static_error = nullptr;  // set by allocation-free entry points
 
 int fail(int status, const std::string &msg)
 {
     g_last_error = msg;
+    g_static_error = nullptr;
     return status;
 }
 
@@ -56,6 +59,10 @@ bool is_device_pointer(const void *p)
 }
 
 }  // namespace
+
+namespace fps {
+void set_static_error(const char *msg) { g_static_error = msg; }
+}  // namespace fps
 
 struct fps_plan {
     int64_t n = 0;
@@ -585,7 +592,7 @@ const char *fps_status_string(int status)
     }
 }
 
-const char *fps_last_error(void) { return g_last_error.c_str(); }
+const char *fps_last_error(void) { return g_static_error ? g_static_error : g_last_error.c_str(); }
 
 int fps_zolotarev_shifts(double a, double b, double c, double d, double tol, int J, int *J_out, double *p, double *q,
                          int cap)

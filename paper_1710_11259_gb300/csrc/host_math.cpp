@@ -118,9 +118,8 @@ int adi_iterations(double a, double b, double c, double d, double tol)
 
 void zolotarev_shifts_symmetric(double lo, double hi, int J, std::vector<double> &q)
 {
-    std::vector<double> dn = dn_at_shift_points(J, lo / hi);
     q.resize(J);
-    for (int j = 0; j < J; ++j) q[j] = hi * dn[j];
+    zolotarev_shifts_symmetric_into(lo, hi, J, q.data());
 }
 
 void zolotarev_shifts(double a, double b, double c, double d, int J, std::vector<double> &p, std::vector<double> &q)
@@ -193,27 +192,8 @@ void square_tight_interval(int64_t n, double &lo, double &hi)
     hi = std::min(1.0, 1.01 * (-l));
 }
 
-// Allocation-free forms of square_bands / inv_sqrt_E / zolotarev_shifts_symmetric
-// (caller-provided arrays; same arithmetic), for the entry point that must not
-// allocate.
-void square_bands_into(int64_t n, double *d, double *e, double *s)
-{
-    for (int64_t j = 0; j < n; ++j) {
-        double x = (double)j;
-        double Ej = (x + 1.0) * (x + 2.0);
-        double Mjj = 2.0 * (x + 1.0) * (x + 2.0) / ((2.0 * x + 1.0) * (2.0 * x + 5.0));
-        d[j] = -Mjj / Ej;
-        e[j] = 0.0;
-        if (j + 2 < n) {
-            double Ej2 = (x + 3.0) * (x + 4.0);
-            double prod4 = (x + 1.0) * (x + 2.0) * (x + 3.0) * (x + 4.0);
-            double Mj2 = -std::sqrt(prod4 * (2.0 * x + 3.0) / (2.0 * x + 7.0)) / ((2.0 * x + 3.0) * (2.0 * x + 5.0));
-            e[j] = -Mj2 / std::sqrt(Ej * Ej2);
-        }
-        s[j] = 1.0 / std::sqrt(((double)j + 1.0) * ((double)j + 2.0));
-    }
-}
-
+// Allocation-free form of zolotarev_shifts_symmetric (caller-provided array), for
+// the entry point that must not allocate; the vector form calls it.
 void zolotarev_shifts_symmetric_into(double lo, double hi, int J, double *q)
 {
     const double kp = lo / hi;

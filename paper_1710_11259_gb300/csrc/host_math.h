@@ -30,8 +30,8 @@ void zolotarev_shifts(double a, double b, double c, double d, int J, std::vector
 // Symmetric case [a,b] = [-hi,-lo], [c,d] = [lo,hi]: q_j = hi * dn(u_j; k' = lo/hi), p_j = -q_j.
 void zolotarev_shifts_symmetric(double lo, double hi, int J, std::vector<double> &q);
 
-// Allocation-free variants writing into caller arrays (d, e, s of length n; q of length J).
-void square_bands_into(int64_t n, double *d, double *e, double *s);
+// Allocation-free variant writing into a caller array q of length J (the vector
+// form above calls it, so both give the same bits).
 void zolotarev_shifts_symmetric_into(double lo, double hi, int J, double *q);
 
 }  // namespace fps

@@ -4,6 +4,7 @@
 // sequential recurrence per system; there is no dense contraction, so no tensor
 // cores are involved.
 #include "kernels.cuh"
+#include "device_info.h"
 
 namespace fps {
 
@@ -325,7 +326,8 @@ cudaError_t launch_scale_out(const double *Y, double *X, const double *s, int64_
 {
     const int64_t nn = n * n;
     int blocks = (int)((nn + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int cap = 16 * current_sm_count();
+    if (blocks > cap) blocks = cap;
     scale_out_kernel<<<blocks, 256, 0, st>>>(Y, X, s, n);
     return cudaGetLastError();
 }

@@ -8,6 +8,8 @@
 // every work array in one file-scope device array of fixed size (kScratchDoubles
 // doubles, 4 MiB) that each GPU loading the library holds until the process exits,
 // and uses only stack memory on the host.  The caller still allocates F and X.
+// Nothing is copied from host memory: the bands of A~ are computed on the device
+// from their closed forms and the shifts reach the device as a kernel argument.
 //
 // Set-up: the device address of the array is looked up with cudaGetSymbolAddress
 // once per device, on the first call made with that device current.  Make that
@@ -20,6 +22,9 @@
 // value a call reads from the array is written earlier by that same call (the
 // zero padding of the band array included), so stale contents never leak into a
 // result.
+//
+// Errors: status codes; fps_last_error() then returns a fixed message naming the
+// check that failed (a pointer to a string literal, so reporting allocates nothing).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,6 +33,7 @@
 #include "../../include/fps.h"
 #include "host_math.h"
 #include "kernels.cuh"
+#include "status.h"
 
 namespace {
 
@@ -41,11 +47,40 @@ constexpr int kMaxDevices = 64;
 double *g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_setup_mutex;
 
-// Errors are reported by status code only (recording a message would allocate).
+// The message is a string literal: recording it allocates nothing.
 int noalloc_fail(int status, const char *why)
 {
-    (void)why;
+    fps::set_static_error(why);
     return status;
+}
+
+// Shifts q_0..q_{J-1} passed by value (2 KiB of kernel parameters).
+struct NoallocShifts {
+    double q[kMaxJ];
+};
+
+// Bands of A~ from the closed forms of (3.7)/(3.9) (the same formulas as the host
+// routine square_bands): d_j = -M_jj / E_j, e_j = -M_{j,j+2} / sqrt(E_j E_{j+2})
+// (zero for j + 2 >= n), s_j = 1/sqrt(E_j), E_j = (j+1)(j+2); and the shift table.
+__global__ void noalloc_bands_kernel(int64_t n, NoallocShifts sh, int J, double *__restrict__ d,
+                                     double *__restrict__ e, double *__restrict__ s, double *__restrict__ q)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < J) q[j] = sh.q[j];
+    if (j >= n) return;
+    const double x = (double)j;
+    const double Ej = (x + 1.0) * (x + 2.0);
+    const double Mjj = 2.0 * (x + 1.0) * (x + 2.0) / ((2.0 * x + 1.0) * (2.0 * x + 5.0));
+    d[j] = -Mjj / Ej;
+    double ej = 0.0;
+    if (j + 2 < n) {
+        const double Ej2 = (x + 3.0) * (x + 4.0);
+        const double prod4 = (x + 1.0) * (x + 2.0) * (x + 3.0) * (x + 4.0);
+        const double Mj2 = -sqrt(prod4 * (2.0 * x + 3.0) / (2.0 * x + 7.0)) / ((2.0 * x + 3.0) * (2.0 * x + 5.0));
+        ej = -Mj2 / sqrt(Ej * Ej2);
+    }
+    e[j] = ej;
+    s[j] = 1.0 / sqrt(Ej);
 }
 
 // Device address of the scratch array on the current device (set up once).
@@ -81,6 +116,23 @@ int fps_poisson_square_solve_noalloc(int64_t n, double tol, const double *F, dou
     const char *f0 = (const char *)F, *x0 = (const char *)X;
     if (f0 < x0 + bytes && x0 < f0 + bytes)
         return noalloc_fail(FPS_ERR_INVALID_ARG, "fps_poisson_square_solve_noalloc: F and X overlap");
+    // Lemma B.2 interval, J of (2.9) and the symmetric shifts (2.4) on the host (the
+    // same routines as the plan, writing into a stack array); the bands of A~
+    // (3.7)/(3.9) are computed on the device below.
+    const double eps = fps::square_eps(n);
+    const int J = fps::adi_iterations(-1.0, -eps, eps, 1.0, tol);
+    if (J < 1 || J > kMaxJ)
+        return noalloc_fail(FPS_ERR_INVALID_ARG, "fps_poisson_square_solve_noalloc: tol needs more than 256 iterations");
+    NoallocShifts sh;
+    fps::zolotarev_shifts_symmetric_into(eps, 1.0, J, sh.q);
+    const double *q = sh.q;
+
+    double *base = nullptr;
+    int dev = 0;
+    int st = scratch_for_current_device(&base, &dev);
+    if (st != FPS_OK) return st;
+    // F and X must be device memory of the current device (where the kernels and the
+    // scratch array run): memory of another GPU would be reached by peer access.
     for (const void *p : {(const void *)F, (const void *)X}) {
         cudaPointerAttributes attr;
         if (cudaPointerGetAttributes(&attr, p) != cudaSuccess ||
@@ -89,24 +141,10 @@ int fps_poisson_square_solve_noalloc(int64_t n, double tol, const double *F, dou
             return noalloc_fail(FPS_ERR_INVALID_ARG,
                                 "fps_poisson_square_solve_noalloc: F and X must be device memory");
         }
+        if (attr.type == cudaMemoryTypeDevice && attr.device != dev)
+            return noalloc_fail(FPS_ERR_INVALID_ARG,
+                                "fps_poisson_square_solve_noalloc: F and X must be on the current device");
     }
-
-    // Lemma B.2 interval, J of (2.9), symmetric shifts (2.4), bands of A~ (3.7)/(3.9):
-    // the same host routines as the plan, writing into stack arrays.
-    const double eps = fps::square_eps(n);
-    const int J = fps::adi_iterations(-1.0, -eps, eps, 1.0, tol);
-    if (J < 1 || J > kMaxJ)
-        return noalloc_fail(FPS_ERR_INVALID_ARG, "fps_poisson_square_solve_noalloc: tol needs more than 256 iterations");
-    double q[kMaxJ];
-    fps::zolotarev_shifts_symmetric_into(eps, 1.0, J, q);
-    double band[3 * kMaxN];
-    double *d = band, *e = band + kMaxN, *s = band + 2 * kMaxN;
-    fps::square_bands_into(n, d, e, s);
-
-    double *base = nullptr;
-    int dev = 0;
-    int st = scratch_for_current_device(&base, &dev);
-    if (st != FPS_OK) return st;
     // Carve the scratch: bands, shifts, factors (J x n double2), then five n x n arrays.
     const int64_t nn = n * n;
     double *d_d = base, *d_e = base + n, *d_s = base + 2 * n, *d_q = base + 3 * n;
@@ -123,10 +161,11 @@ int fps_poisson_square_solve_noalloc(int64_t n, double tol, const double *F, dou
     do {                                                                                                 \
         if ((call) != cudaSuccess) return noalloc_fail(FPS_ERR_CUDA, "fps_poisson_square_solve_noalloc: " #call); \
     } while (0)
-    NA_CK(cudaMemcpyAsync(d_d, d, sizeof(double) * n, cudaMemcpyHostToDevice, strm));
-    NA_CK(cudaMemcpyAsync(d_e, e, sizeof(double) * n, cudaMemcpyHostToDevice, strm));
-    NA_CK(cudaMemcpyAsync(d_s, s, sizeof(double) * n, cudaMemcpyHostToDevice, strm));
-    NA_CK(cudaMemcpyAsync(d_q, q, sizeof(double) * J, cudaMemcpyHostToDevice, strm));
+    {
+        const int64_t m = n > J ? n : (int64_t)J;
+        noalloc_bands_kernel<<<(unsigned)((m + 127) / 128), 128, 0, strm>>>(n, sh, J, d_d, d_e, d_s, d_q);
+        NA_CK(cudaGetLastError());
+    }
     NA_CK(fps::launch_factors(d_d, d_e, d_q, J, n, fac, strm));
     NA_CK(fps::launch_scale_in(F, Ft, FtT, d_s, n, strm));
     for (int j = 0; j < J; ++j) {

@@ -149,3 +149,34 @@ def test_legendre_conversion_argument_errors(L):
     assert L.fps_solution_to_legendre(2, p, None, None) == -1
     assert L.fps_solution_to_legendre(2, p, p, None) == -1         # X inside U
     assert b"overlap" in L.fps_last_error()
+
+
+def test_binding_rejects_mismatched_buffers():
+    """The binding checks shapes before handing raw pointers to the library, so a
+    wrong-sized tensor can never make a kernel run past the end of a buffer."""
+    plan = api.Plan(0, 8, 2, 1)                      # shape (8, 8); no library call
+    with pytest.raises(api.FpsError) as e:
+        api._check_plan_buffers(plan, np.zeros((8, 9)), np.zeros((8, 9)))
+    assert e.value.status == -1
+    with pytest.raises(api.FpsError):
+        api._check_plan_buffers(plan, np.zeros((2, 8, 8)), np.zeros((2, 8, 8)))
+    with pytest.raises(api.FpsError):
+        api._check_plan_buffers(plan, np.zeros((8, 8)), np.zeros((7, 8)))
+    api._check_plan_buffers(plan, np.zeros((8, 8)), np.zeros((8, 8)))
+    api._check_plan_buffers(plan, np.zeros(64), np.zeros(64))          # packed form
+    cube = api.Plan(0, 4, 3, 2)
+    api._check_plan_buffers(cube, np.zeros((2, 4, 4, 4)), np.zeros(128))
+    with pytest.raises(api.FpsError):
+        api._check_plan_buffers(cube, np.zeros((4, 4, 4)), np.zeros(64))
+    batch = api.Plan(0, 5, 2, 2, batch_ns=np.array([5, 3]))
+    api._check_plan_buffers(batch, np.zeros(2 * 34), np.zeros(2 * 34))
+    with pytest.raises(api.FpsError):
+        api._check_plan_buffers(batch, np.zeros(2 * 34 - 1), np.zeros(2 * 34))
+
+
+def test_noalloc_binding_rejects_non_square(L):
+    for F, X in [(np.zeros((4, 5)), np.zeros((4, 5))), (np.zeros(16), np.zeros(16)),
+                 (np.zeros((4, 4)), np.zeros((5, 5))), (np.zeros((2, 4, 4)), np.zeros((2, 4, 4)))]:
+        with pytest.raises(api.FpsError) as e:
+            api.poisson_square_solve_noalloc(F, X)
+        assert e.value.status == -1

@@ -9,6 +9,7 @@ run stopping at the first failure has already run every other test."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1710_11259_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -50,10 +51,35 @@ def test_noalloc_matches_plan_solve_twice(api, n):
         assert err <= TOL_FP64, f"call {call}: rel-max diff {err:.3e}"
 
 
+def test_noalloc_matches_oracle_n64(api):
+    """Independent of the plan's kernels: the n = 64 right-hand side with decay
+    1/((1+j)^2(1+k)^2) (seed 0) against the CPU oracle at the FP64 bar."""
+    Fh = inputs.square_rhs(64, 0)
+    F = torch.from_numpy(Fh).cuda()
+    X = torch.full_like(F, float("nan"))
+    assert api.poisson_square_solve_noalloc(F, X, 1e-13) == 0
+    torch.cuda.synchronize()
+    Xo = oracle.poisson_square(Fh, 1e-13)
+    err = float(np.abs(X.cpu().numpy() - Xo).max() / np.abs(Xo).max())
+    assert err <= TOL_FP64, err
+
+
 def test_noalloc_rejects_oversize_and_host_buffers(api):
     F = torch.zeros(257, 257, dtype=torch.float64, device="cuda")
     X = torch.zeros_like(F)
     assert api.poisson_square_solve_noalloc(F, X, 1e-13) == -1
+    assert "n must be in [1, 256]" in api.lib().fps_last_error().decode()
     Fh = np.zeros((16, 16))
     Xh = np.zeros((16, 16))
     assert api.poisson_square_solve_noalloc(Fh, Xh, 1e-13) == -1
+    assert "device memory" in api.lib().fps_last_error().decode()
+
+
+def test_noalloc_rejects_buffers_of_another_device(api):
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    F = torch.zeros(16, 16, dtype=torch.float64, device="cuda:1")
+    X = torch.zeros_like(F)
+    with torch.cuda.device(0):
+        assert api.lib().fps_poisson_square_solve_noalloc(16, 1e-13, F.data_ptr(), X.data_ptr(), None) == -1
+    assert "current device" in api.lib().fps_last_error().decode()
