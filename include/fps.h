@@ -151,28 +151,40 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info);
 /*
  * fps_plan_shifts -- copy the plan's ADI shifts q_0..q_{J-1} (for the square,
  * p_j = -q_j) into q (capacity `cap`); returns the count written or a negative
- * status.  For a batch, the shifts of problem `problem`.
+ * status.  FPS_FP64: the shifts of the solve (Lemma B.2 interval, J of (2.9)).
+ * FPS_FP32_REFINE: the shifts of the finest inner level (tight interval of A~,
+ * tolerance 1e-7) of problem `problem` (0 unless batched).
  */
 int fps_plan_shifts(const fps_plan *plan, int64_t problem, double *q, int cap);
 
 /*
  * fps_plan_set_instrument -- on != 0: record CUDA events around every launch of
- * the plan's dominant kernel (FP64: the half-step sweep; FP32_REFINE: the column
- * back-substitution pass), inside the captured graphs, so that its duration can
- * be read after a solve without changing what runs.  Rebuilds the graphs.
- * Errors: INVALID_ARG, CUDA.
+ * the plan's ADI pass kernels (the row pass and the column pass of every
+ * iteration of Algorithm 2), inside the captured graphs, so that their duration
+ * can be read after a solve without changing what runs.  Rebuilds the graphs.
+ * Square plans only.  Errors: INVALID_ARG, UNSUPPORTED (cube plan), CUDA.
  */
 int fps_plan_set_instrument(fps_plan *plan, int on);
 
 /*
  * fps_plan_kernel_times -- for the last solve of an instrumented plan: number of
- * timed launches of the dominant kernel (*count), their summed duration in ms
- * (*total_ms) and the algorithmic bytes they move (*alg_bytes: the arrays each
- * launch must read and write, 8 bytes per FP64 and 4 per FP32 element; no
- * scratch, halo or re-read traffic).  Synchronises the plan's stream.
- * Errors: INVALID_ARG (not instrumented), CUDA.
+ * timed launches of the ADI pass kernels (*count, two per iteration), their summed
+ * duration in ms (*total_ms) and the algorithmic bytes they move (*alg_bytes: per
+ * element and iteration the residual-form ADI reads and writes six n x n words --
+ * the row pass reads c and D and writes D and its result, the column pass reads
+ * that result and writes c -- four in the first iteration, five in the second;
+ * 8 bytes per FP64 and 4 per FP32 word; no padding, halo, segment-summary or
+ * re-read traffic).  Synchronises the plan's stream.
+ * Errors: INVALID_ARG (not instrumented), TIMEOUT (a bounded device wait gave up), CUDA.
  */
 int fps_plan_kernel_times(fps_plan *plan, int *count, double *total_ms, double *alg_bytes);
+
+/*
+ * fps_plan_pass_times -- the summed durations (ms) of the row passes and of the
+ * column passes of the last solve of an instrumented plan (their sum is the
+ * *total_ms of fps_plan_kernel_times).  Errors as fps_plan_kernel_times.
+ */
+int fps_plan_pass_times(fps_plan *plan, double *row_ms, double *col_ms);
 
 /*
  * fps_legendre_to_ctilde -- Legendre coefficients in (Sec. 3.4, Table 3.1 step 1):

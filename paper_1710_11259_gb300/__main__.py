@@ -23,6 +23,7 @@ def main() -> None:
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--power", type=int, default=2)
+    ap.add_argument("--instrument", action="store_true", help="time the ADI pass kernels (square plans)")
     a = ap.parse_args()
 
     import torch
@@ -38,6 +39,8 @@ def main() -> None:
         F = torch.from_numpy(inputs.cube_rhs(a.n, a.seed, power=a.power)).cuda()
         solve = api.poisson_cube_solve
     plan = api.plan_create(a.n, a.dim, tol, a.precision)
+    if a.instrument:
+        api.plan_set_instrument(plan, True)
     X = solve(plan, F)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -47,6 +50,8 @@ def main() -> None:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(a.reps, 1)
     info = api.plan_info(plan)
+    if a.instrument:
+        info["pass_kernels"] = api.plan_kernel_times(plan)
     api.plan_destroy(plan)
     print(json.dumps({"n": a.n, "dim": a.dim, "precision": a.precision, "tol": tol,
                       "ms_per_solve": ms if a.reps > 0 else None,

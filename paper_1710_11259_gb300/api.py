@@ -66,7 +66,7 @@ EXPORTED = [
     "fps_poisson_cube_solve", "fps_poisson_adjoint", "fps_plan_info", "fps_plan_shifts", "fps_plan_destroy",
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
     "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
-    "fps_square_spectral_interval", "fps_legendre_to_ctilde", "fps_solution_to_legendre",
+    "fps_square_spectral_interval", "fps_legendre_to_ctilde", "fps_solution_to_legendre", "fps_plan_pass_times",
 ]
 
 
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         L.fps_square_bands.argtypes = [i64, dp, dp]
         L.fps_plan_set_instrument.argtypes = [vp, ctypes.c_int]
         L.fps_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
+        L.fps_plan_pass_times.argtypes = [vp, dp, dp]
         L.fps_poisson_square_solve_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp]
         L.fps_square_spectral_interval.argtypes = [i64, ctypes.c_int, dp, dp]
         L.fps_legendre_to_ctilde.argtypes = [i64, vp, vp, vp]
@@ -274,7 +275,9 @@ def plan_kernel_times(plan: Plan) -> dict:
     ms = ctypes.c_double()
     by = ctypes.c_double()
     _check(lib().fps_plan_kernel_times(plan.handle, ctypes.byref(c), ctypes.byref(ms), ctypes.byref(by)))
-    return {"count": c.value, "total_ms": ms.value, "alg_bytes": by.value}
+    rm, cm = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fps_plan_pass_times(plan.handle, ctypes.byref(rm), ctypes.byref(cm)))
+    return {"count": c.value, "total_ms": ms.value, "alg_bytes": by.value, "row_ms": rm.value, "col_ms": cm.value}
 
 
 def plan_destroy(plan: Plan) -> None:

@@ -9,8 +9,7 @@
 
 #include "../../include/fps.h"
 #include "host_math.h"
-#include "kernels.cuh"
-#include "refine_engine.h"
+#include "sweep_engine.h"
 #include "cube.h"
 #include "legendre.cuh"
 #include "trace.h"
@@ -72,58 +71,40 @@ struct fps_plan {
     int nrhs = 1;
     int device = 0;
     cudaStream_t stream = nullptr;      // user stream
-    cudaStream_t cap_stream = nullptr;  // private stream used to capture the graph
+    cudaStream_t cap_stream = nullptr;  // private stream used to capture the graphs
 
     int J = 0;
-    std::vector<double> q;  // shifts q_j > 0 (p_j = -q_j)
-
-    // device data
-    double *d_d = nullptr, *d_e = nullptr, *d_s = nullptr, *d_q = nullptr;
-    double2 *d_fac = nullptr;
-    double *Ft = nullptr, *FtT = nullptr, *A = nullptr, *B = nullptr, *Z = nullptr;
+    std::vector<double> q;  // shifts q_j > 0 of the FP64 solve (p_j = -q_j)
     int64_t bytes = 0;
 
-    cudaGraphExec_t graph = nullptr;
-    int refine_rounds = 0;
-    double last_residual = 0;
-
-    // FPS_FP32_REFINE (single problem or batch): the refinement engine
-    fps::RefineEngine *eng = nullptr;
+    // square: the ADI pass engine (FP32 sweeps + FP64 refinement, or plain FP64)
+    fps::SweepEngine<float> *eng32 = nullptr;
+    fps::SweepEngine<double> *eng64 = nullptr;
     // dim = 3: the nested cube ADI
     fps::CubeEngine *cube = nullptr;
     std::vector<int64_t> batch_ns;   // sizes of a batched plan (empty otherwise)
     int64_t total_elems = 0;         // doubles in F (and X) for all right-hand sides / problems
     double *stage_in = nullptr, *stage_out = nullptr;  // lazily allocated for host pointers
 
-    // instrumentation and accounting (FP64 path)
     bool instrument = false;
-    std::vector<cudaEvent_t> ev64;          // FP64: 2 per half-step
     int64_t launches_last = 0;
 };
 
 namespace {
 
-template <typename T>
-cudaError_t dmalloc(fps_plan *p, T **ptr, size_t count)
-{
-    cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * (count ? count : 1));
-    if (e == cudaSuccess) p->bytes += (int64_t)(sizeof(T) * count);
-    return e;
-}
-
 void release(fps_plan *p)
 {
     if (!p) return;
     DeviceGuard g(p->device);
-    if (p->graph) cudaGraphExecDestroy(p->graph);
-    void *bufs[] = {p->d_d, p->d_e, p->d_s, p->d_q, p->d_fac, p->Ft, p->FtT, p->A, p->B, p->Z, p->stage_in,
-                    p->stage_out};
-    for (void *b : bufs)
-        if (b) cudaFree(b);
-    for (cudaEvent_t e : p->ev64) cudaEventDestroy(e);
-    if (p->eng) {
-        p->eng->release();
-        delete p->eng;
+    if (p->stage_in) cudaFree(p->stage_in);
+    if (p->stage_out) cudaFree(p->stage_out);
+    if (p->eng32) {
+        p->eng32->release();
+        delete p->eng32;
+    }
+    if (p->eng64) {
+        p->eng64->release();
+        delete p->eng64;
     }
     if (p->cube) {
         p->cube->release();
@@ -133,76 +114,9 @@ void release(fps_plan *p)
     delete p;
 }
 
-// Enqueue the 2J half-steps of Algorithm 2 (FP64) from F~, F~^T to Y_J (normal
-// orientation) in p->B.  Buffers: A holds Y_{j+1/2} (normal), B holds Y_j^T.
-cudaError_t enqueue_adi_fp64(fps_plan *p, cudaStream_t st)
-{
-    const int64_t n = p->n;
-    for (int j = 0; j < p->J; ++j) {
-        fps::HalfStep<double> h;
-        h.d = p->d_d;
-        h.e = p->d_e;
-        h.q = p->q[j];
-        h.n = n;
-        h.Z = p->Z;
-        h.fac = p->d_fac + (int64_t)j * n;
-        // step 1 (transposed form): (A~ - q) Y_h^T = F~^T - Y^T (A~ + q); store Y_h
-        h.V = (j == 0) ? nullptr : p->B;
-        h.G = p->FtT;
-        h.Out = p->A;
-        h.transposed_out = true;
-        const bool ins = p->instrument && (int)p->ev64.size() == 4 * p->J;
-        cudaError_t e;
-        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-        e = fps::launch_halfstep(h, st);
-        if (e != cudaSuccess) return e;
-        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j + 1], st, cudaEventRecordExternal)) != cudaSuccess)
-            return e;
-        // step 2: (A~ - q) Y^+ = F~ - Y_h (A~ + q); store (Y^+)^T, or Y_J itself last
-        h.V = p->A;
-        h.G = p->Ft;
-        h.Out = p->B;
-        h.transposed_out = (j + 1 < p->J);
-        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j + 2], st, cudaEventRecordExternal)) != cudaSuccess)
-            return e;
-        e = fps::launch_halfstep(h, st);
-        if (e != cudaSuccess) return e;
-        if (ins && (e = cudaEventRecordWithFlags(p->ev64[4 * j + 3], st, cudaEventRecordExternal)) != cudaSuccess)
-            return e;
-    }
-    return cudaSuccess;
-}
-
-int build_graph(fps_plan *p)
-{
-    FPS_CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_adi_fp64(p, p->cap_stream);
-    cudaGraph_t g = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
-    if (e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return fail(FPS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    }
-    FPS_CK(e2);
-    e = cudaGraphInstantiate(&p->graph, g, 0);
-    cudaGraphDestroy(g);
-    FPS_CK(e);
-    return FPS_OK;
-}
-
-// One right-hand side, device pointers (FP64 path).
-int solve_one(fps_plan *p, const double *F, double *X)
-{
-    cudaStream_t st = p->stream;
-    FPS_CK(fps::launch_scale_in(F, p->Ft, p->FtT, p->d_s, p->n, st));
-    FPS_CK(cudaGraphLaunch(p->graph, st));
-    FPS_CK(fps::launch_scale_out(p->B, X, p->d_s, p->n, st));
-    p->launches_last += 2LL * p->J + 2;
-    return FPS_OK;
-}
-
-// FP32_REFINE (single or batched): the whole packed F at once.
-int solve_engine(fps_plan *p, const double *F, double *X, bool fdev, bool xdev, const char *what)
+// The whole packed F at once (every problem and right-hand side of the plan).
+template <typename E>
+int solve_engine(fps_plan *p, E *eng, const double *F, double *X, bool fdev, bool xdev, const char *what)
 {
     const size_t bytes = sizeof(double) * (size_t)p->total_elems;
     const double *Fd = F;
@@ -217,14 +131,17 @@ int solve_engine(fps_plan *p, const double *F, double *X, bool fdev, bool xdev, 
         Xd = p->stage_out;
     }
     std::string err;
-    const int st = p->eng->solve(Fd, Xd, p->stream, err);
+    const int st = eng->solve(Fd, Xd, p->stream, err);
     if (st != FPS_OK && st != FPS_ERR_NOT_CONVERGED) return fail(st, std::string(what) + ": " + err);
-    p->launches_last = p->eng->launches_last;
+    p->launches_last = eng->launches_last;
     if (!xdev) {
         FPS_CK(cudaMemcpyAsync(X, Xd, bytes, cudaMemcpyDeviceToHost, p->stream));
         FPS_CK(cudaStreamSynchronize(p->stream));
+    } else if (!fdev) {
+        FPS_CK(cudaStreamSynchronize(p->stream));  // host F must stay valid only until copied
     }
     if (st != FPS_OK) return fail(st, std::string(what) + ": " + err);
+    FPS_CK(cudaGetLastError());
     return FPS_OK;
 }
 
@@ -240,27 +157,8 @@ int solve_square(fps_plan *p, const double *F, double *X, const char *what)
     DeviceGuard g(p->device);
     const bool fdev = is_device_pointer(F), xdev = is_device_pointer(X);
     p->launches_last = 0;
-    if (p->eng) return solve_engine(p, F, X, fdev, xdev, what);
-    const int64_t nn = p->n * p->n;
-    for (int r = 0; r < p->nrhs; ++r) {
-        const double *Fr = F + (int64_t)r * nn;
-        double *Xr = X + (int64_t)r * nn;
-        const double *Fd = Fr;
-        if (!fdev) {
-            FPS_CK(cudaMemcpyAsync(p->B, Fr, sizeof(double) * nn, cudaMemcpyHostToDevice, p->stream));
-            Fd = p->B;
-        }
-        double *Xd = xdev ? Xr : p->A;
-        int s = solve_one(p, Fd, Xd);
-        if (s != FPS_OK) return s;
-        if (!xdev) {
-            FPS_CK(cudaMemcpyAsync(Xr, p->A, sizeof(double) * nn, cudaMemcpyDeviceToHost, p->stream));
-            FPS_CK(cudaStreamSynchronize(p->stream));
-        }
-    }
-    if (!fdev && xdev) FPS_CK(cudaStreamSynchronize(p->stream));  // host F must stay valid only until copied
-    FPS_CK(cudaGetLastError());
-    return FPS_OK;
+    if (p->eng32) return solve_engine(p, p->eng32, F, X, fdev, xdev, what);
+    return solve_engine(p, p->eng64, F, X, fdev, xdev, what);
 }
 
 }  // namespace
@@ -332,43 +230,21 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     const double eps = fps::square_eps(n);
     p->J = fps::adi_iterations(-1.0, -eps, eps, 1.0, tol);
     fps::zolotarev_shifts_symmetric(eps, 1.0, p->J, p->q);
-    std::vector<double> d, e, s;
-    fps::square_bands(n, d, e);
-    fps::inv_sqrt_E(n, s);
-
-    const size_t nn = (size_t)n * (size_t)n;
+    if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the square supports n <= 40000"));
+    if (nrhs > 256) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the square supports nrhs <= 256"));
     PCK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
-    PCK(dmalloc(p, &p->d_d, n));
-    PCK(dmalloc(p, &p->d_e, n));
-    PCK(dmalloc(p, &p->d_s, n));
-    PCK(dmalloc(p, &p->d_q, p->J));
+    std::string err;
+    int st;
     if (precision == FPS_FP64) {
-        PCK(dmalloc(p, &p->Ft, nn));
-        PCK(dmalloc(p, &p->d_fac, (size_t)p->J * n));
-        PCK(dmalloc(p, &p->FtT, nn));
-        PCK(dmalloc(p, &p->A, nn));
-        PCK(dmalloc(p, &p->B, nn));
-        PCK(dmalloc(p, &p->Z, nn));
-    }
-    PCK(cudaMemcpyAsync(p->d_d, d.data(), sizeof(double) * n, cudaMemcpyHostToDevice, p->cap_stream));
-    PCK(cudaMemcpyAsync(p->d_e, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice, p->cap_stream));
-    PCK(cudaMemcpyAsync(p->d_s, s.data(), sizeof(double) * n, cudaMemcpyHostToDevice, p->cap_stream));
-    PCK(cudaMemcpyAsync(p->d_q, p->q.data(), sizeof(double) * p->J, cudaMemcpyHostToDevice, p->cap_stream));
-    if (precision == FPS_FP64) {
-        PCK(fps::launch_factors(p->d_d, p->d_e, p->d_q, p->J, n, p->d_fac, p->cap_stream));
-        PCK(cudaStreamSynchronize(p->cap_stream));
-        int st = build_graph(p);
-        if (st != FPS_OK) return bail(st);
+        p->eng64 = new fps::SweepEngine<double>();
+        st = p->eng64->create(std::vector<int64_t>{n}, nrhs, tol, false, p->cap_stream, err);
+        if (st == FPS_OK) p->bytes += p->eng64->bytes;
     } else {
-        if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: FP32_REFINE supports n <= 40000"));
-        if (nrhs > 256) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: FP32_REFINE supports nrhs <= 256"));
-        PCK(cudaStreamSynchronize(p->cap_stream));
-        p->eng = new fps::RefineEngine();
-        std::string err;
-        const int st = p->eng->create(std::vector<int64_t>{n}, nrhs, tol, p->cap_stream, 0, err);
-        if (st != FPS_OK) return bail(fail(st, "fps_plan_create: " + err));
-        p->bytes += p->eng->bytes;
+        p->eng32 = new fps::SweepEngine<float>();
+        st = p->eng32->create(std::vector<int64_t>{n}, nrhs, tol, true, p->cap_stream, err);
+        if (st == FPS_OK) p->bytes += p->eng32->bytes;
     }
+    if (st != FPS_OK) return bail(fail(st, "fps_plan_create: " + err));
 #undef PCK
     *out = p;
     return FPS_OK;
@@ -409,14 +285,14 @@ int fps_plan_create_batched(fps_plan **out, const int64_t *ns, int64_t count, in
         delete p;
         return fail(FPS_ERR_CUDA, "fps_plan_create_batched: stream creation failed");
     }
-    p->eng = new fps::RefineEngine();
+    p->eng32 = new fps::SweepEngine<float>();
     std::string err;
-    const int st = p->eng->create(v, nrhs, tol, p->cap_stream, 0, err);
+    const int st = p->eng32->create(v, nrhs, tol, true, p->cap_stream, err);
     if (st != FPS_OK) {
         release(p);
         return fail(st, "fps_plan_create_batched: " + err);
     }
-    p->bytes += p->eng->bytes;
+    p->bytes += p->eng32->bytes;
     *out = p;
     return FPS_OK;
 }
@@ -491,9 +367,9 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->nrhs = plan->nrhs;
     info->batch = plan->batch_ns.empty() ? 1 : (int64_t)plan->batch_ns.size();
     info->J = plan->J;
-    info->J_inner = plan->eng ? plan->eng->J_inner_first : 0;
-    info->refine_rounds = plan->eng ? plan->eng->rounds_last : 0;
-    info->last_residual = plan->eng ? plan->eng->resid_last : 0.0;
+    info->J_inner = plan->eng32 ? plan->eng32->J_first : 0;
+    info->refine_rounds = plan->eng32 ? plan->eng32->rounds_last : 0;
+    info->last_residual = plan->eng32 ? plan->eng32->resid_last : 0.0;
     if (plan->cube) {
         info->J_inner = plan->cube->J_outer_inner;
         info->refine_rounds = plan->cube->rounds_last;
@@ -503,68 +379,63 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->tol = plan->tol;
     info->device_bytes = plan->bytes;
     info->kernel_launches = plan->launches_last;
-    info->pass_ctas = plan->eng ? plan->eng->chosen_target_ctas : 0;
+    info->pass_ctas = 0;
     return FPS_OK;
 }
 
 int fps_plan_set_instrument(fps_plan *p, int on)
 {
     if (!p) return fail(FPS_ERR_INVALID_ARG, "fps_plan_set_instrument: plan is NULL");
+    if (!p->eng32 && !p->eng64) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_set_instrument: square plans only");
     DeviceGuard g(p->device);
     FPS_CK(cudaStreamSynchronize(p->cap_stream));
     if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));
     else FPS_CK(cudaDeviceSynchronize());
     p->instrument = on != 0;
-    if (p->eng) {
-        std::string err;
-        const int st = p->eng->set_instrument(p->instrument, err);
-        return st == FPS_OK ? FPS_OK : fail(st, "fps_plan_set_instrument: " + err);
-    }
-    for (cudaEvent_t e : p->ev64) cudaEventDestroy(e);
-    p->ev64.clear();
-    if (p->instrument) {
-        p->ev64.resize(4 * (size_t)p->J);
-        for (auto &e : p->ev64) FPS_CK(cudaEventCreate(&e));
-    }
-    if (p->graph) cudaGraphExecDestroy(p->graph);
-    p->graph = nullptr;
-    return build_graph(p);
+    std::string err;
+    const int st = p->eng32 ? p->eng32->set_instrument(p->instrument, err) : p->eng64->set_instrument(p->instrument, err);
+    return st == FPS_OK ? FPS_OK : fail(st, "fps_plan_set_instrument: " + err);
 }
+
+namespace {
+int pass_times(fps_plan *p, int *count, double *total_ms, double *alg_bytes, double *row_ms, double *col_ms,
+               const char *what)
+{
+    if (!p->instrument) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": plan is not instrumented");
+    DeviceGuard g(p->device);
+    if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));
+    else FPS_CK(cudaDeviceSynchronize());
+    std::string err;
+    const int st = p->eng32 ? p->eng32->kernel_times(count, total_ms, alg_bytes, row_ms, col_ms, err)
+                            : p->eng64->kernel_times(count, total_ms, alg_bytes, row_ms, col_ms, err);
+    return st == FPS_OK ? FPS_OK : fail(st, std::string(what) + ": " + err);
+}
+}  // namespace
 
 int fps_plan_kernel_times(fps_plan *p, int *count, double *total_ms, double *alg_bytes)
 {
     if (!p || !count || !total_ms || !alg_bytes) return fail(FPS_ERR_INVALID_ARG, "fps_plan_kernel_times: NULL argument");
-    if (!p->instrument) return fail(FPS_ERR_INVALID_ARG, "fps_plan_kernel_times: plan is not instrumented");
-    DeviceGuard g(p->device);
-    if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));
-    else FPS_CK(cudaDeviceSynchronize());
-    if (p->eng) {
-        std::string err;
-        const int st = p->eng->kernel_times(count, total_ms, alg_bytes, err);
-        return st == FPS_OK ? FPS_OK : fail(st, "fps_plan_kernel_times: " + err);
-    }
-    const double nn = (double)p->n * (double)p->n;
+    return pass_times(p, count, total_ms, alg_bytes, nullptr, nullptr, "fps_plan_kernel_times");
+}
+
+int fps_plan_pass_times(fps_plan *p, double *row_ms, double *col_ms)
+{
+    if (!p || !row_ms || !col_ms) return fail(FPS_ERR_INVALID_ARG, "fps_plan_pass_times: NULL argument");
     int c = 0;
-    double ms = 0.0, bytes = 0.0;
-    for (int k = 0; k < 2 * p->J; ++k) {
-        float t = 0.f;
-        FPS_CK(cudaEventElapsedTime(&t, p->ev64[2 * k], p->ev64[2 * k + 1]));
-        ms += t;
-        ++c;
-        bytes += (k == 0 ? 2.0 : 3.0) * 8.0 * nn;  // V (unless zero), G read; W written
-    }
-    *count = c;
-    *total_ms = ms;
-    *alg_bytes = bytes;
-    return FPS_OK;
+    double t = 0.0, b = 0.0;
+    return pass_times(p, &c, &t, &b, row_ms, col_ms, "fps_plan_pass_times");
 }
 
 int fps_plan_shifts(const fps_plan *plan, int64_t problem, double *q, int cap)
 {
-    if (!plan || !q || problem != 0) return fail(FPS_ERR_INVALID_ARG, "fps_plan_shifts: bad argument");
-    if (cap < plan->J) return fail(FPS_ERR_INVALID_ARG, "fps_plan_shifts: capacity too small");
-    std::memcpy(q, plan->q.data(), sizeof(double) * plan->J);
-    return plan->J;
+    if (!plan || !q) return fail(FPS_ERR_INVALID_ARG, "fps_plan_shifts: bad argument");
+    const std::vector<double> *v = &plan->q;
+    const int64_t count = plan->batch_ns.empty() ? 1 : (int64_t)plan->batch_ns.size();
+    if (problem < 0 || problem >= count) return fail(FPS_ERR_INVALID_ARG, "fps_plan_shifts: bad problem index");
+    if (plan->eng32) v = &plan->eng32->shifts[problem];
+    if (cap < (int)v->size()) return fail(FPS_ERR_INVALID_ARG, "fps_plan_shifts: capacity too small");
+    std::memcpy(q, v->data(), sizeof(double) * v->size());
+    return (int)v->size();
 }
 
 void fps_plan_destroy(fps_plan *plan)

@@ -1,0 +1,873 @@
+// ADI pass kernels of the square solve (see sweep.cuh for the scheme and layout).
+//
+// Tiles travel through shared memory by bulk asynchronous copies (cp.async.bulk,
+// one copy per tile row, completion on an mbarrier; results leave by bulk stores),
+// so no thread spends registers or issue slots on address streams.  Inside a tile
+// every thread owns one line (a row in the row pass, a column in the column pass)
+// and keeps the whole segment of that line in registers: two interleaved
+// recurrences (even and odd positions, App. B) per thread, no shared-memory
+// traffic during the sweeps.
+#include <cuda_runtime.h>
+
+#include "bulk.cuh"
+#include "sweep.cuh"
+
+namespace fps {
+
+namespace {
+
+constexpr int kR = 64;    // rows per row-pass tile (= threads)
+constexpr int kC = 64;    // columns per column-pass tile (= threads)
+constexpr int kChainLines = 128;
+
+// 16-byte chunks of T
+template <typename T>
+struct Ch {
+    static constexpr int V = 16 / sizeof(T);
+};
+
+template <typename T>
+__device__ __forceinline__ void ld16(const T *p, T (&v)[16 / sizeof(T)]);
+template <>
+__device__ __forceinline__ void ld16<float>(const float *p, float (&v)[4])
+{
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    v[0] = f.x;
+    v[1] = f.y;
+    v[2] = f.z;
+    v[3] = f.w;
+}
+template <>
+__device__ __forceinline__ void ld16<double>(const double *p, double (&v)[2])
+{
+    const double2 f = *reinterpret_cast<const double2 *>(p);
+    v[0] = f.x;
+    v[1] = f.y;
+}
+template <typename T>
+__device__ __forceinline__ void st16(T *p, const T (&v)[16 / sizeof(T)]);
+template <>
+__device__ __forceinline__ void st16<float>(float *p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st16<double>(double *p, const double (&v)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type mk2(T x, T y);
+template <>
+__device__ __forceinline__ float2 mk2<float>(float x, float y)
+{
+    return make_float2(x, y);
+}
+template <>
+__device__ __forceinline__ double2 mk2<double>(double x, double y)
+{
+    return make_double2(x, y);
+}
+
+// Shared-memory row stride of the row-pass tile: S + 8 loaded columns plus padding
+// that makes the stride an odd number of 16-byte chunks (conflict-free 16-byte
+// accesses by threads that own consecutive rows).
+template <typename T, int S>
+struct RowGeom {
+    static constexpr int V = Ch<T>::V;
+    static constexpr int SW = S + 8 + V;
+    static_assert((SW * sizeof(T) / 16) % 2 == 1, "row stride must be an odd number of 16-byte chunks");
+    static constexpr size_t off_ct = 16;
+    static constexpr size_t off_zx = off_ct + sizeof(T) * (kR + 4) * SW;
+    static constexpr size_t off_frow = off_zx + sizeof(typename Vec2<T>::type) * 6 * (S + 8);
+    static constexpr size_t off_fcol = off_frow + sizeof(Fac<T>) * (kR + 4);
+    static constexpr size_t off_coef = off_fcol + sizeof(Fac<T>) * S;
+    static constexpr size_t bytes = off_coef + sizeof(T) * 3 * S;
+    static_assert(off_zx % 16 == 0 && off_frow % 16 == 0 && off_fcol % 16 == 0 && off_coef % 16 == 0, "alignment");
+};
+
+template <typename T, int S>
+struct ColGeom {
+    static constexpr int ZS = S + 2;  // padded stride of the two parity rows of zx
+    static constexpr size_t off_tile = 16;
+    static constexpr size_t off_fac = off_tile + sizeof(T) * S * kC;
+    static constexpr size_t off_zx = off_fac + sizeof(Fac<T>) * S;
+    static constexpr size_t bytes = off_zx + sizeof(typename Vec2<T>::type) * 2 * ZS;
+    static_assert(off_fac % 16 == 0 && off_zx % 16 == 0, "alignment");
+};
+
+// ---------------------------------------------------------------------------
+// Shift tables: one thread per (job, parity), FP64 arithmetic.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void fac_tables_kernel(const FacJob<T> *__restrict__ jobs, int njobs)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= 2 * njobs) return;
+    const FacJob<T> &jb = jobs[tid >> 1];
+    const int p = tid & 1;
+    const int n = jb.n, N = jb.N, S = jb.S;
+    Fac<T> *out = jb.out + 2;  // position i at out[i]
+    // forward: pivots of the parity-p tridiagonal of A~ - qI, and phi within segments
+    double piv_prev = 1.0, phi = 1.0;
+    for (int i = p; i < N; i += 2) {
+        double ip = 0.0, g = 0.0, uf = 0.0;
+        if (i < n) {
+            const double em2 = (i >= 2) ? jb.e[i - 2] : 0.0;
+            double piv = jb.d[i] - jb.q;
+            if (i >= 2) piv -= em2 * em2 / piv_prev;
+            ip = 1.0 / piv;
+            g = em2 * ip;
+            uf = jb.e[i] * ip;
+            piv_prev = piv;
+        }
+        if ((i - p) % S == 0) phi = 1.0;  // first parity-p position of a segment
+        phi *= -g;
+        Fac<T> f;
+        f.ip = (T)ip;
+        f.g = (T)g;
+        f.uf = (T)uf;
+        f.phi = (T)phi;
+        f.Bv = 0;
+        f.Psi = 0;
+        out[i] = f;
+    }
+    // backward within each segment: Bv_i = phi_i - uf_i Bv_{i+2}, Psi_i = -uf_i Psi_{i+2}
+    double Bv = 0.0, Psi = 1.0;
+    for (int i = N - 2 + p; i >= p; i -= 2) {
+        if (i + 2 >= N || ((i + 2 - p) % S) == 0) {  // last parity-p position of its segment
+            Bv = 0.0;
+            Psi = 1.0;
+        }
+        const double uf = (double)out[i].uf;
+        Bv = (double)out[i].phi - uf * Bv;
+        Psi = -uf * Psi;
+        out[i].Bv = (T)Bv;
+        out[i].Psi = (T)Psi;
+    }
+}
+
+// Bounded wait on the tile barrier; on a timeout flag the error word and give the
+// copies in flight one more bounded wait before the CTA leaves.
+__device__ __forceinline__ bool tile_ready(uint64_t *bar, int *err)
+{
+    if (bulk::mbar_wait_bounded(bar, 0)) return true;
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    bulk::mbar_wait_bounded(bar, 0);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Row pass.  Item {problem, rhs, row block (64 rows), column segment}.
+// MODE 0: j = 0, input rho_0.  MODE 1: j = 1, D = -2 q_0 c_0.  MODE 2: D -= 2 q_{j-1} c_{j-1}.
+// ---------------------------------------------------------------------------
+template <typename T, int S, int MODE>
+__global__ void __launch_bounds__(kR) row_pass_kernel(SwArgs<T> a, int j)
+{
+    using G = RowGeom<T, S>;
+    using T2 = typename Vec2<T>::type;
+    constexpr int V = G::V, SW = G::SW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    T *ct = reinterpret_cast<T *>(smem + G::off_ct);
+    T2 *zx = reinterpret_cast<T2 *>(smem + G::off_zx);
+    Fac<T> *frow = reinterpret_cast<Fac<T> *>(smem + G::off_frow);
+    Fac<T> *fcol = reinterpret_cast<Fac<T> *>(smem + G::off_fcol);
+    T *cA = reinterpret_cast<T *>(smem + G::off_coef);
+    T *cB = cA + S;
+    T *cC = cB + S;
+
+    const int4 it = a.items[blockIdx.x];
+    const SwProb<T> &pr = a.probs[it.x];
+    if (!a.active[it.x] || j >= pr.J) return;
+    const int tid = threadIdx.x;
+    // after a timeout anywhere, leave at once (one read, agreed on by the whole CTA)
+    if (__syncthreads_or(tid == 0 ? *(volatile int *)a.err : 0)) return;
+    const int N = pr.N, ldp = pr.ldp;
+    const int i0 = it.z * kR, cs = it.w, k0 = cs * S;
+    const int Wc = min(S, N - k0);
+    const int64_t base = pr.off + (int64_t)it.y * pr.rhs;
+    const T *src = (MODE == 0 ? a.rho0 : a.cl) + base;
+    T *Dp = a.D + base;
+    T *alp = a.al + base;
+    const int64_t sbase = pr.soff + (int64_t)it.y * pr.srhs;
+    const Fac<T> *facj = pr.fac + (int64_t)j * (N + 4);
+    const Fac<T> *facp = pr.fac + (int64_t)(MODE > 0 ? j - 1 : 0) * (N + 4);
+    const T qprev = MODE > 0 ? pr.q[j - 1] : T(0);
+
+    // column segments of the halo rows (row systems of the previous column pass)
+    const int sc = i0 / S, segstart = sc * S, segend = min(segstart + S, N);
+    const int s_above = (MODE > 0 && i0 == segstart && i0 > 0) ? sc - 1 : -1;
+    const int s_below = (MODE > 0 && i0 + kR == segend && segend < N) ? sc + 1 : -1;
+    const int rows_ld = MODE == 0 ? kR : kR + 4;
+    const int row0 = MODE == 0 ? i0 : i0 - 2;   // first global row loaded
+    const int smr0 = MODE == 0 ? 2 : 0;          // its shared-memory row
+    const int cw = MODE == 0 ? Wc : Wc + 8;      // loaded columns
+    const int kc0 = MODE == 0 ? k0 : k0 - 4;     // first loaded column
+    const int scc0 = MODE == 0 ? 4 : 0;          // its shared-memory column
+
+    if (tid == 0) {
+        bulk::mbar_init(bar, 1);
+        bulk::fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned bytes = (unsigned)(rows_ld * cw * sizeof(T) + Wc * sizeof(Fac<T>));
+        if (MODE > 0)
+            bytes += (unsigned)((kR + 4) * sizeof(Fac<T>) +
+                                2 * cw * sizeof(T2) * (1 + (s_above >= 0) + (s_below >= 0)));
+        bulk::mbar_arrive_expect_tx(bar, bytes);
+    }
+    __syncthreads();
+    for (int r = tid; r < rows_ld; r += kR)
+        bulk::g2s(ct + (smr0 + r) * SW + scc0, src + (int64_t)(row0 + r + 2) * ldp + (kc0 + 4),
+                  (unsigned)(cw * sizeof(T)), bar);
+    if (tid == kR - 1) bulk::g2s(fcol, facj + k0 + 2, (unsigned)(Wc * sizeof(Fac<T>)), bar);
+    if (MODE > 0) {
+        if (tid == kR - 2) bulk::g2s(frow, facp + i0, (unsigned)((kR + 4) * sizeof(Fac<T>)), bar);
+        if (tid >= kR - 8 && tid < kR - 2) {
+            const int k = tid - (kR - 8), slot = k >> 1, par = k & 1;
+            const int sg = slot == 0 ? s_above : (slot == 1 ? sc : s_below);
+            if (sg >= 0)
+                bulk::g2s(zx + (slot * 2 + par) * (S + 8), a.zxC + sbase + ((int64_t)sg * 2 + par) * (N + 8) + k0,
+                          (unsigned)(cw * sizeof(T2)), bar);
+        }
+        bulk::prefetch_l2(Dp + (int64_t)(i0 + tid + 2) * ldp + (k0 + 4), (unsigned)(Wc * sizeof(T)));
+    }
+    if (!tile_ready(bar, a.err)) return;
+
+    // ip-scaled row-stencil coefficients of this tile's columns
+    for (int c = tid; c < Wc; c += kR) {
+        const int k = k0 + c;
+        const T ipk = fcol[c].ip;
+        if (MODE > 0) {
+            cA[c] = ipk * pr.e[k];               // e_{k-2}
+            cB[c] = ipk * (pr.d[k + 2] + qprev);
+            cC[c] = ipk * pr.e[k + 2];           // e_k
+        } else {
+            cB[c] = ipk;
+        }
+    }
+    if (MODE > 0) {
+        // rebuild c_{j-1} = cl + Bv zin + Psi xout on the whole loaded tile; D update on its core
+        const T q2 = T(2) * qprev;
+        const int cpr = cw / V;
+        const int total = (kR + 4) * cpr;
+        for (int idx = tid; idx < total; idx += kR) {
+            const int r = idx / cpr, cc = (idx - r * cpr) * V;
+            const int i = i0 - 2 + r;
+            T *cp = ct + r * SW + cc;
+            T v[V];
+            ld16(cp, v);
+            if (i >= 0 && i < N) {
+                const int slot = i < segstart ? 0 : (i >= segend ? 2 : 1);
+                const T2 *z = zx + (slot * 2 + (i & 1)) * (S + 8) + cc;
+                const T bv = frow[r].Bv, ps = frow[r].Psi;
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const T2 zz = z[e];
+                    v[e] = fma(bv, zz.x, fma(ps, zz.y, v[e]));
+                }
+                st16(cp, v);
+                if (r >= 2 && r < kR + 2 && cc >= 4 && cc < Wc + 4) {
+                    T *dp = Dp + (int64_t)(i + 2) * ldp + (k0 + cc);
+                    T dv[V];
+                    if (MODE == 1) {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) dv[e] = -q2 * v[e];
+                    } else {
+                        ld16(dp, dv);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) dv[e] = fma(-q2, v[e], dv[e]);
+                    }
+                    st16(dp, dv);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // one thread per row: rho' = ip * (R + q)(L + q) c (or ip * rho_0), forward sweep
+    const int r = tid + 2;
+    const int i = i0 + tid;
+    T wr[S];
+    T we0 = 0, we1 = 0;
+    {
+        T w0 = 0, w1 = 0;
+        if (MODE == 0) {
+#pragma unroll
+            for (int m = 0; m < S / V; ++m) {
+                if (m * V < Wc) {
+                    T v[V], b[V];
+                    ld16(ct + r * SW + 4 + m * V, v);
+                    ld16(cB + m * V, b);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int c = m * V + e;
+                        const T g = fcol[c].g;
+                        if (e & 1) {
+                            w1 = fma(-g, w1, b[e] * v[e]);
+                            wr[c] = w1;
+                        } else {
+                            w0 = fma(-g, w0, b[e] * v[e]);
+                            wr[c] = w0;
+                        }
+                        if (c == Wc - 2) we0 = w0;
+                        if (c == Wc - 1) we1 = w1;
+                    }
+                }
+            }
+        } else {
+            const T eu = pr.e[i], dq = pr.d[i + 2] + qprev, ed = pr.e[i + 2];
+            const T *r0 = ct + (r - 2) * SW, *r1 = ct + r * SW, *r2 = ct + (r + 2) * SW;
+            // window of column-stencil values u = (L + q) c over three chunks
+            T U[3 * V];
+            auto ucol = [&](int q, T *dst) {
+                T x0[V], x1[V], x2[V];
+                ld16(r0 + q * V, x0);
+                ld16(r1 + q * V, x1);
+                ld16(r2 + q * V, x2);
+#pragma unroll
+                for (int e = 0; e < V; ++e) dst[e] = fma(eu, x0[e], fma(dq, x1[e], ed * x2[e]));
+            };
+            constexpr int q0 = 4 / V;  // chunk of shared column 4 (local column 0)
+            ucol(q0 - 1, U);
+            ucol(q0, U + V);
+#pragma unroll
+            for (int m = 0; m < S / V; ++m) {
+                if (m * V < Wc) {
+                    const int q = q0 + m;
+                    ucol(q + 1, U + 2 * V);
+                    T ca[V], cb[V], cc[V];
+                    ld16(cA + m * V, ca);
+                    ld16(cB + m * V, cb);
+                    ld16(cC + m * V, cc);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int c = m * V + e;
+                        const T rho = fma(ca[e], U[V + e - 2], fma(cb[e], U[V + e], cc[e] * U[V + e + 2]));
+                        const T g = fcol[c].g;
+                        if (e & 1) {
+                            w1 = fma(-g, w1, rho);
+                            wr[c] = w1;
+                        } else {
+                            w0 = fma(-g, w0, rho);
+                            wr[c] = w0;
+                        }
+                        if (c == Wc - 2) we0 = w0;
+                        if (c == Wc - 1) we1 = w1;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 2 * V; ++e) U[e] = U[e + V];
+                }
+            }
+        }
+    }
+    // back substitution (local: zero beyond the segment)
+    {
+        T x0 = 0, x1 = 0;
+#pragma unroll
+        for (int c = S - 1; c >= 0; --c) {
+            if (c < Wc) {
+                const T uf = fcol[c].uf;
+                if (c & 1) {
+                    x1 = fma(-uf, x1, wr[c]);
+                    wr[c] = x1;
+                } else {
+                    x0 = fma(-uf, x0, wr[c]);
+                    wr[c] = x0;
+                }
+            }
+        }
+    }
+    const bool live = i < pr.n;
+    __syncthreads();  // every thread is done reading the tile
+#pragma unroll
+    for (int m = 0; m < S / V; ++m) {
+        if (m * V < Wc) {
+            T v[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[e] = live ? wr[m * V + e] : T(0);
+            st16(ct + r * SW + 4 + m * V, v);
+        }
+    }
+    {
+        typename Vec2<T>::type *sm = a.sumR + sbase;
+        sm[((int64_t)cs * 2 + 0) * (N + 8) + i + 4] = mk2<T>(live ? we0 : T(0), live ? wr[0] : T(0));
+        sm[((int64_t)cs * 2 + 1) * (N + 8) + i + 4] = mk2<T>(live ? we1 : T(0), live ? wr[1] : T(0));
+    }
+    bulk::fence_proxy_async_shared();
+    __syncthreads();
+    bulk::s2g(alp + (int64_t)(i + 2) * ldp + (k0 + 4), ct + r * SW + 4, (unsigned)(Wc * sizeof(T)));
+    bulk::commit();
+    bulk::wait_read_all();
+}
+
+// ---------------------------------------------------------------------------
+// Column pass.  Item {problem, rhs, column block (64 columns), row segment}.
+// ---------------------------------------------------------------------------
+template <typename T, int S>
+__global__ void __launch_bounds__(kC) col_pass_kernel(SwArgs<T> a, int j)
+{
+    using G = ColGeom<T, S>;
+    using T2 = typename Vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    T *tile = reinterpret_cast<T *>(smem + G::off_tile);
+    Fac<T> *fac = reinterpret_cast<Fac<T> *>(smem + G::off_fac);
+    T2 *zx = reinterpret_cast<T2 *>(smem + G::off_zx);
+
+    const int4 it = a.items[blockIdx.x];
+    const SwProb<T> &pr = a.probs[it.x];
+    if (!a.active[it.x] || j >= pr.J) return;
+    const int tid = threadIdx.x;
+    // after a timeout anywhere, leave at once (one read, agreed on by the whole CTA)
+    if (__syncthreads_or(tid == 0 ? *(volatile int *)a.err : 0)) return;
+    const int N = pr.N, ldp = pr.ldp;
+    const int k0 = it.z * kC, rs = it.w, i0 = rs * S;
+    const int Hr = min(S, N - i0);
+    const int cs = k0 / S;  // row-system segment holding these columns
+    const int64_t base = pr.off + (int64_t)it.y * pr.rhs;
+    const int64_t sbase = pr.soff + (int64_t)it.y * pr.srhs;
+    const Fac<T> *facj = pr.fac + (int64_t)j * (N + 4);
+
+    if (tid == 0) {
+        bulk::mbar_init(bar, 1);
+        bulk::fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        bulk::mbar_arrive_expect_tx(bar, (unsigned)(Hr * kC * sizeof(T) + Hr * sizeof(Fac<T>) + 2 * Hr * sizeof(T2)));
+    __syncthreads();
+    for (int r = tid; r < Hr; r += kC)
+        bulk::g2s(tile + r * kC, a.al + base + (int64_t)(i0 + r + 2) * ldp + (k0 + 4), (unsigned)(kC * sizeof(T)), bar);
+    if (tid == kC - 1) bulk::g2s(fac, facj + i0 + 2, (unsigned)(Hr * sizeof(Fac<T>)), bar);
+    if (tid == kC - 2 || tid == kC - 3) {
+        const int par = kC - 2 - tid;
+        bulk::g2s(zx + par * G::ZS, a.zxR + sbase + ((int64_t)cs * 2 + par) * (N + 8) + i0 + 4,
+                  (unsigned)(Hr * sizeof(T2)), bar);
+    }
+    const int k = k0 + tid;
+    const Fac<T> fk = facj[k + 2];
+    const T2 *zp = zx + (k & 1) * G::ZS;
+    if (!tile_ready(bar, a.err)) return;
+
+    T wr[S];
+    T we0 = 0, we1 = 0;
+    {
+        T w0 = 0, w1 = 0;
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            if (r < Hr) {
+                const T2 z = zp[r];
+                const T av = fma(fk.Bv, z.x, fma(fk.Psi, z.y, tile[r * kC + tid]));
+                const T ip = fac[r].ip, g = fac[r].g;
+                if (r & 1) {
+                    w1 = fma(-g, w1, ip * av);
+                    wr[r] = w1;
+                } else {
+                    w0 = fma(-g, w0, ip * av);
+                    wr[r] = w0;
+                }
+                if (r == Hr - 2) we0 = w0;
+                if (r == Hr - 1) we1 = w1;
+            }
+        }
+    }
+    {
+        T x0 = 0, x1 = 0;
+#pragma unroll
+        for (int r = S - 1; r >= 0; --r) {
+            if (r < Hr) {
+                const T uf = fac[r].uf;
+                if (r & 1) {
+                    x1 = fma(-uf, x1, wr[r]);
+                    wr[r] = x1;
+                } else {
+                    x0 = fma(-uf, x0, wr[r]);
+                    wr[r] = x0;
+                }
+            }
+        }
+    }
+    const bool live = k < pr.n;
+#pragma unroll
+    for (int r = 0; r < S; ++r)
+        if (r < Hr) tile[r * kC + tid] = live ? wr[r] : T(0);
+    {
+        T2 *sm = a.sumC + sbase;
+        sm[((int64_t)rs * 2 + 0) * (N + 8) + k + 4] = mk2<T>(live ? we0 : T(0), live ? wr[0] : T(0));
+        sm[((int64_t)rs * 2 + 1) * (N + 8) + k + 4] = mk2<T>(live ? we1 : T(0), live ? wr[1] : T(0));
+    }
+    bulk::fence_proxy_async_shared();
+    __syncthreads();
+    for (int r = tid; r < Hr; r += kC)
+        bulk::s2g(a.cl + base + (int64_t)(i0 + r + 2) * ldp + (k0 + 4), tile + r * kC, (unsigned)(kC * sizeof(T)));
+    bulk::commit();
+    bulk::wait_read_all();
+}
+
+// ---------------------------------------------------------------------------
+// Chains: true forward value entering and true solution leaving every segment.
+// Item {problem, rhs, block of 128 lines}; thread = (line, parity).
+//   W_s = wl_end(s) + phi_end(s) W_{s-1},           zin(s)  = W_{s-1}
+//   X_s = xl_start(s) + Bv_start(s) zin(s) + Psi_start(s) X_{s+1},   xout(s) = X_{s+1}
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(2 * kChainLines) chain_kernel(SwArgs<T> a, int dir, int j)
+{
+    using T2 = typename Vec2<T>::type;
+    const int4 it = a.items[blockIdx.x];
+    const SwProb<T> &pr = a.probs[it.x];
+    if (!a.active[it.x] || j >= pr.J) return;
+    const int p = threadIdx.x / kChainLines;
+    const int l = it.z * kChainLines + (threadIdx.x % kChainLines);
+    const int N = pr.N, S = pr.S, P = pr.P;
+    if (l >= N) return;
+    const int64_t sbase = pr.soff + (int64_t)it.y * pr.srhs;
+    const T2 *sum = (dir == 0 ? a.sumR : a.sumC) + sbase;
+    T2 *zx = (dir == 0 ? a.zxR : a.zxC) + sbase;
+    T *zs = a.zin + sbase;
+    const Fac<T> *facj = pr.fac + (int64_t)j * (N + 4) + 2;
+    T W = 0;
+#pragma unroll 4
+    for (int s = 0; s < P; ++s) {
+        const int64_t idx = ((int64_t)s * 2 + p) * (N + 8) + l + 4;
+        const T2 sm = sum[idx];
+        const int pe = min(s * S + S, N) - 2 + p;
+        zs[idx] = W;
+        W = fma(facj[pe].phi, W, sm.x);
+    }
+    T X = 0;
+#pragma unroll 4
+    for (int s = P - 1; s >= 0; --s) {
+        const int64_t idx = ((int64_t)s * 2 + p) * (N + 8) + l + 4;
+        const T2 sm = sum[idx];
+        const T zi = zs[idx];
+        const Fac<T> fb = facj[s * S + p];
+        zx[idx] = mk2<T>(zi, X);
+        X = fma(fb.Bv, zi, fma(fb.Psi, X, sm.y));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise kernels over 32 x 32 tiles of the n x n region.
+// ---------------------------------------------------------------------------
+struct TileView {
+    int n, ldp, prob, rhs, pair;
+    int64_t off64, offT;
+    const double *d, *e, *s;
+    int bx, by;
+};
+__device__ __forceinline__ TileView tile_view(const TileArgs &t)
+{
+    const int4 q = t.tiles[blockIdx.x];
+    const TileProb &p = t.probs[q.x >> 8];
+    TileView v;
+    v.prob = q.x >> 8;
+    v.rhs = q.x & 255;
+    v.n = p.n;
+    v.ldp = p.ldp;
+    v.off64 = p.off64 + (int64_t)v.rhs * p.n * p.n;
+    v.offT = p.off + (int64_t)v.rhs * p.rhs;
+    v.d = p.d;
+    v.e = p.e;
+    v.s = p.s;
+    v.pair = p.pair0 + v.rhs;
+    v.bx = q.y * 32;
+    v.by = q.z * 32;
+    return v;
+}
+
+// c_{J-1} at (i, k) rebuilt from the column pass's local result and its chain.
+template <typename T>
+__device__ __forceinline__ T rebuilt_c(const SwArgs<T> &a, const SwProb<T> &pr, int64_t offT, int64_t sbase,
+                                       const Fac<T> &fi, int i, int k)
+{
+    const T cl = a.cl[offT + (int64_t)(i + 2) * pr.ldp + k + 4];
+    const typename Vec2<T>::type z = a.zxC[sbase + ((int64_t)(i / pr.S) * 2 + (i & 1)) * (pr.N + 8) + k + 4];
+    return fma(fi.Bv, z.x, fma(fi.Psi, z.y, cl));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) finalize_kernel(TileArgs t, SwArgs<T> a, const int *__restrict__ pair_active)
+{
+    const TileView v = tile_view(t);
+    if (!pair_active[v.pair]) return;
+    const SwProb<T> &pr = a.probs[v.prob];
+    const int J = pr.J;
+    const T q2 = T(2) * pr.q[J - 1];
+    const Fac<T> *fac = pr.fac + (int64_t)(J - 1) * (pr.N + 4) + 2;
+    const int64_t sbase = pr.soff + (int64_t)v.rhs * pr.srhs;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = v.by + r, k = v.bx + threadIdx.x;
+        if (i < v.n && k < v.n) {
+            const T c = rebuilt_c(a, pr, v.offT, sbase, fac[i], i, k);
+            T *dp = a.D + v.offT + (int64_t)(i + 2) * pr.ldp + k + 4;
+            *dp = (J >= 2) ? fma(-q2, c, *dp) : -q2 * c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) finalize_out_kernel(TileArgs t, SwArgs<double> a, double *__restrict__ X)
+{
+    const TileView v = tile_view(t);
+    const SwProb<double> &pr = a.probs[v.prob];
+    if (!a.active[v.prob]) return;
+    const int J = pr.J;
+    const double q2 = 2.0 * pr.q[J - 1];
+    const Fac<double> *fac = pr.fac + (int64_t)(J - 1) * (pr.N + 4) + 2;
+    const int64_t sbase = pr.soff + (int64_t)v.rhs * pr.srhs;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = v.by + r, k = v.bx + threadIdx.x;
+        if (i < v.n && k < v.n) {
+            const double c = rebuilt_c(a, pr, v.offT, sbase, fac[i], i, k);
+            const double y = (J >= 2) ? fma(-q2, c, a.D[v.offT + (int64_t)(i + 2) * pr.ldp + k + 4]) : -q2 * c;
+            X[v.off64 + (int64_t)i * v.n + k] = y * v.s[i] * v.s[k];
+        }
+    }
+}
+
+__device__ __forceinline__ double flag_nonfinite(double x, double local)
+{
+    // NaN and Inf both become +Inf so that the maximum flags them (fmax drops NaN)
+    return (x <= 1.7976931348623157e308) ? fmax(local, x) : __longlong_as_double(0x7ff0000000000000LL);
+}
+
+__device__ __forceinline__ void block_max_to(double local, unsigned long long *out)
+{
+    for (int off = 16; off > 0; off >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, off));
+    __shared__ double wmax[8];
+    if (threadIdx.x == 0) wmax[threadIdx.y] = local;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double bm = 0.0;
+        for (int q = 0; q < (int)blockDim.y; ++q) bm = fmax(bm, wmax[q]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(bm));
+    }
+}
+
+__global__ void __launch_bounds__(256) absmax_kernel(TileArgs t, const double *__restrict__ F,
+                                                     unsigned long long *__restrict__ smax)
+{
+    const TileView v = tile_view(t);
+    double local = 0.0;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = v.by + r, k = v.bx + threadIdx.x;
+        if (i < v.n && k < v.n) local = flag_nonfinite(fabs(F[v.off64 + (int64_t)i * v.n + k] * v.s[i] * v.s[k]), local);
+    }
+    block_max_to(local, smax + v.pair);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) scale_in_kernel(TileArgs t, const double *__restrict__ F, double *__restrict__ Ft,
+                                                       T *__restrict__ rho0, const unsigned long long *__restrict__ smax)
+{
+    const TileView v = tile_view(t);
+    double inv = 1.0;
+    if (smax) {
+        const double sF = __longlong_as_double((long long)smax[v.pair]);
+        inv = sF > 0.0 ? 1.0 / sF : 0.0;
+    }
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = v.by + r, k = v.bx + threadIdx.x;
+        if (i < v.n && k < v.n) {
+            const double val = F[v.off64 + (int64_t)i * v.n + k] * v.s[i] * v.s[k];
+            if (Ft) Ft[v.off64 + (int64_t)i * v.n + k] = val;
+            rho0[v.offT + (int64_t)(i + 2) * v.ldp + k + 4] = (T)(val * inv);
+        }
+    }
+}
+
+// Yout = Y + s D; R = F~ - A~ Yout - Yout A~; rho0 = R / s; rmax = max |R|.
+// Y and Yout are distinct buffers, so every CTA sees the same not-yet-updated halo.
+__global__ void __launch_bounds__(256) residual_kernel(TileArgs t, const double *__restrict__ Y,
+                                                       double *__restrict__ Yout, const float *__restrict__ D,
+                                                       const double *__restrict__ Ft, float *__restrict__ rho0,
+                                                       const unsigned long long *__restrict__ smax,
+                                                       unsigned long long *__restrict__ rmax,
+                                                       const int *__restrict__ pair_active, int y_zero)
+{
+    __shared__ double Ys[36][37];
+    const TileView v = tile_view(t);
+    const int n = v.n;
+    if (!pair_active[v.pair]) {
+        for (int r = threadIdx.y; r < 32; r += 8) {
+            const int i = v.by + r, k = v.bx + threadIdx.x;
+            if (i < n && k < n) Yout[v.off64 + (int64_t)i * n + k] = y_zero ? 0.0 : Y[v.off64 + (int64_t)i * n + k];
+        }
+        return;
+    }
+    const double sF = __longlong_as_double((long long)smax[v.pair]);
+    const double inv = sF > 0.0 ? 1.0 / sF : 0.0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 36; r += 8) {
+        const int i = v.by - 2 + r;
+        for (int cc = tx; cc < 36; cc += 32) {
+            const int k = v.bx - 2 + cc;
+            double val = 0.0;
+            if (i >= 0 && i < n && k >= 0 && k < n) {
+                val = y_zero ? 0.0 : Y[v.off64 + (int64_t)i * n + k];
+                val = fma(sF, (double)D[v.offT + (int64_t)(i + 2) * v.ldp + k + 4], val);
+            }
+            Ys[r][cc] = val;
+        }
+    }
+    __syncthreads();
+    double local = 0.0;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = v.by + r, k = v.bx + tx;
+        if (i < n && k < n) {
+            const double y = Ys[r + 2][tx + 2];
+            double acc = Ft[v.off64 + (int64_t)i * n + k];
+            acc = fma(-(v.d[i] + v.d[k]), y, acc);
+            if (i >= 2) acc = fma(-v.e[i - 2], Ys[r][tx + 2], acc);
+            acc = fma(-v.e[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
+            if (k >= 2) acc = fma(-v.e[k - 2], Ys[r + 2][tx], acc);
+            acc = fma(-v.e[k], Ys[r + 2][tx + 4], acc);
+            Yout[v.off64 + (int64_t)i * n + k] = y;
+            local = flag_nonfinite(fabs(acc), local);
+            rho0[v.offT + (int64_t)(i + 2) * v.ldp + k + 4] = (float)(acc * inv);
+        }
+    }
+    block_max_to(local, rmax + v.pair);
+}
+
+__global__ void __launch_bounds__(256) scale_out_kernel(TileArgs t, const double *__restrict__ Y, double *__restrict__ X)
+{
+    const TileView v = tile_view(t);
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = v.by + r, k = v.bx + threadIdx.x;
+        if (i < v.n && k < v.n)
+            X[v.off64 + (int64_t)i * v.n + k] = Y[v.off64 + (int64_t)i * v.n + k] * v.s[i] * v.s[k];
+    }
+}
+
+template <typename T>
+struct SegLen;
+template <>
+struct SegLen<float> {
+    static constexpr int S = 128;
+};
+template <>
+struct SegLen<double> {
+    static constexpr int S = 64;
+};
+
+}  // namespace
+
+int sweep_segment_length(bool fp64) { return fp64 ? SegLen<double>::S : SegLen<float>::S; }
+
+cudaError_t sweep_setup_kernels()
+{
+    cudaError_t e;
+#define SETSM(kern, bytes)                                                                                \
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))) !=    \
+        cudaSuccess)                                                                                      \
+        return e;
+    SETSM((row_pass_kernel<float, 128, 0>), (RowGeom<float, 128>::bytes));
+    SETSM((row_pass_kernel<float, 128, 1>), (RowGeom<float, 128>::bytes));
+    SETSM((row_pass_kernel<float, 128, 2>), (RowGeom<float, 128>::bytes));
+    SETSM((row_pass_kernel<double, 64, 0>), (RowGeom<double, 64>::bytes));
+    SETSM((row_pass_kernel<double, 64, 1>), (RowGeom<double, 64>::bytes));
+    SETSM((row_pass_kernel<double, 64, 2>), (RowGeom<double, 64>::bytes));
+    SETSM((col_pass_kernel<float, 128>), (ColGeom<float, 128>::bytes));
+    SETSM((col_pass_kernel<double, 64>), (ColGeom<double, 64>::bytes));
+#undef SETSM
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_fac_tables(const FacJob<T> *jobs, int njobs, cudaStream_t st)
+{
+    const int threads = 2 * njobs;
+    fac_tables_kernel<T><<<(threads + 127) / 128, 128, 0, st>>>(jobs, njobs);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_row_pass(const SwArgs<T> &a, int j, int mode, cudaStream_t st)
+{
+    constexpr int S = SegLen<T>::S;
+    const size_t sm = RowGeom<T, S>::bytes;
+    const dim3 grid((unsigned)a.nitems);
+    if (mode == 0) row_pass_kernel<T, S, 0><<<grid, kR, sm, st>>>(a, j);
+    else if (mode == 1) row_pass_kernel<T, S, 1><<<grid, kR, sm, st>>>(a, j);
+    else row_pass_kernel<T, S, 2><<<grid, kR, sm, st>>>(a, j);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_col_pass(const SwArgs<T> &a, int j, cudaStream_t st)
+{
+    constexpr int S = SegLen<T>::S;
+    col_pass_kernel<T, S><<<(unsigned)a.nitems, kC, ColGeom<T, S>::bytes, st>>>(a, j);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_chain(const SwArgs<T> &a, int dir, int j, cudaStream_t st)
+{
+    chain_kernel<T><<<(unsigned)a.nitems, 2 * kChainLines, 0, st>>>(a, dir, j);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_finalize(const TileArgs &t, const SwArgs<T> &a, const int *pair_active, cudaStream_t st)
+{
+    finalize_kernel<T><<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, a, pair_active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_out(const TileArgs &t, const SwArgs<double> &a, double *X, cudaStream_t st)
+{
+    finalize_out_kernel<<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, a, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const TileArgs &t, const double *F, unsigned long long *smax, cudaStream_t st)
+{
+    absmax_kernel<<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, F, smax);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale_in(const TileArgs &t, const double *F, double *Ft, T *rho0, const unsigned long long *smax,
+                            cudaStream_t st)
+{
+    scale_in_kernel<T><<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, F, Ft, rho0, smax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const TileArgs &t, const double *Y, double *Yout, const float *D, const double *Ft,
+                            float *rho0, const unsigned long long *smax, unsigned long long *rmax,
+                            const int *pair_active, bool y_zero, cudaStream_t st)
+{
+    residual_kernel<<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, Y, Yout, D, Ft, rho0, smax, rmax, pair_active,
+                                                               y_zero ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_out(const TileArgs &t, const double *Y, double *X, cudaStream_t st)
+{
+    scale_out_kernel<<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, Y, X);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fac_tables<float>(const FacJob<float> *, int, cudaStream_t);
+template cudaError_t launch_fac_tables<double>(const FacJob<double> *, int, cudaStream_t);
+template cudaError_t launch_row_pass<float>(const SwArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_row_pass<double>(const SwArgs<double> &, int, int, cudaStream_t);
+template cudaError_t launch_col_pass<float>(const SwArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_col_pass<double>(const SwArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_chain<float>(const SwArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_chain<double>(const SwArgs<double> &, int, int, cudaStream_t);
+template cudaError_t launch_finalize<float>(const TileArgs &, const SwArgs<float> &, const int *, cudaStream_t);
+template cudaError_t launch_finalize<double>(const TileArgs &, const SwArgs<double> &, const int *, cudaStream_t);
+template cudaError_t launch_scale_in<float>(const TileArgs &, const double *, double *, float *,
+                                            const unsigned long long *, cudaStream_t);
+template cudaError_t launch_scale_in<double>(const TileArgs &, const double *, double *, double *,
+                                             const unsigned long long *, cudaStream_t);
+
+}  // namespace fps
