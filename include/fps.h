@@ -73,8 +73,9 @@ typedef struct {
     double tol;             /* requested tolerance */
     int64_t device_bytes;   /* device memory owned by the plan */
     int64_t kernel_launches; /* kernels of this library launched by the last solve */
-    int pass_ctas;          /* FP32_REFINE: CTAs per pass aimed at on the largest problem
-                               (picked by the autotuner unless FPS_AUTOTUNE=0) */
+    int seg_len;            /* square plans: segment length of the partitioned sweeps (rows of a
+                               column-pass tile, columns of a row-pass tile); FP32_REFINE: picked
+                               by the autotuner unless FPS_AUTOTUNE=0 */
     int64_t inner_iterations; /* cube: inner (slice Stein) ADI iterations over full
                                  tensors in the last solve, all levels and rounds */
 } fps_plan_info_t;

@@ -53,7 +53,7 @@ class PlanInfo(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("device_bytes", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
-        ("pass_ctas", ctypes.c_int),
+        ("seg_len", ctypes.c_int),
         ("inner_iterations", ctypes.c_int64),
     ]
 

@@ -16,9 +16,11 @@ namespace fps {
 
 namespace {
 
-constexpr int kR = 64;    // rows per row-pass tile (= threads)
-constexpr int kC = 64;    // columns per column-pass tile (= threads)
-constexpr int kChainLines = 128;
+constexpr int kR = 64;    // rows per row-pass tile
+constexpr int kC = 64;    // columns per column-pass tile
+constexpr int kRT = 128;  // row-pass threads: one per (row, parity of the column index)
+constexpr int kCT = 128;  // column-pass threads: one per (column, parity of the row index)
+constexpr int kChainLines = 64;
 
 // 16-byte chunks of T
 template <typename T>
@@ -56,6 +58,24 @@ __device__ __forceinline__ void st16<double>(double *p, const double (&v)[2])
 {
     *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
 }
+// four consecutive words (16-byte aligned) as one or two vector loads
+__device__ __forceinline__ void ld4(const float *p, float &a, float &b, float &c, float &d)
+{
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    a = f.x;
+    b = f.y;
+    c = f.z;
+    d = f.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double &a, double &b, double &c, double &d)
+{
+    const double2 f = *reinterpret_cast<const double2 *>(p);
+    const double2 h = *reinterpret_cast<const double2 *>(p + 2);
+    a = f.x;
+    b = f.y;
+    c = h.x;
+    d = h.y;
+}
 
 template <typename T>
 __device__ __forceinline__ typename Vec2<T>::type mk2(T x, T y);
@@ -82,9 +102,9 @@ struct RowGeom {
     static constexpr size_t off_zx = off_ct + sizeof(T) * (kR + 4) * SW;
     static constexpr size_t off_frow = off_zx + sizeof(typename Vec2<T>::type) * 6 * (S + 8);
     static constexpr size_t off_fcol = off_frow + sizeof(Fac<T>) * (kR + 4);
-    static constexpr size_t off_coef = off_fcol + sizeof(Fac<T>) * S;
-    static constexpr size_t bytes = off_coef + sizeof(T) * 3 * S;
-    static_assert(off_zx % 16 == 0 && off_frow % 16 == 0 && off_fcol % 16 == 0 && off_coef % 16 == 0, "alignment");
+    static constexpr size_t off_cf = off_fcol + sizeof(Fac<T>) * S;  // {cA, cB, cC, g} per column
+    static constexpr size_t bytes = off_cf + sizeof(T) * 4 * S;
+    static_assert(off_zx % 16 == 0 && off_frow % 16 == 0 && off_fcol % 16 == 0 && off_cf % 16 == 0, "alignment");
 };
 
 template <typename T, int S>
@@ -161,32 +181,25 @@ __device__ __forceinline__ bool tile_ready(uint64_t *bar, int *err)
 // ---------------------------------------------------------------------------
 // Row pass.  Item {problem, rhs, row block (64 rows), column segment}.
 // MODE 0: j = 0, input rho_0.  MODE 1: j = 1, D = -2 q_0 c_0.  MODE 2: D -= 2 q_{j-1} c_{j-1}.
+// W: columns of this tile's segment (S, or 64 for a short last segment).
 // ---------------------------------------------------------------------------
-template <typename T, int S, int MODE>
-__global__ void __launch_bounds__(kR) row_pass_kernel(SwArgs<T> a, int j)
+template <typename T, int S, int MODE, int W>
+__device__ __forceinline__ void row_pass_tile(const SwArgs<T> &a, int j, const int4 it, const SwProb<T> &pr,
+                                              unsigned char *smem)
 {
     using G = RowGeom<T, S>;
     using T2 = typename Vec2<T>::type;
     constexpr int V = G::V, SW = G::SW;
-    extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     T *ct = reinterpret_cast<T *>(smem + G::off_ct);
     T2 *zx = reinterpret_cast<T2 *>(smem + G::off_zx);
     Fac<T> *frow = reinterpret_cast<Fac<T> *>(smem + G::off_frow);
     Fac<T> *fcol = reinterpret_cast<Fac<T> *>(smem + G::off_fcol);
-    T *cA = reinterpret_cast<T *>(smem + G::off_coef);
-    T *cB = cA + S;
-    T *cC = cB + S;
+    T *cf = reinterpret_cast<T *>(smem + G::off_cf);
 
-    const int4 it = a.items[blockIdx.x];
-    const SwProb<T> &pr = a.probs[it.x];
-    if (!a.active[it.x] || j >= pr.J) return;
     const int tid = threadIdx.x;
-    // after a timeout anywhere, leave at once (one read, agreed on by the whole CTA)
-    if (__syncthreads_or(tid == 0 ? *(volatile int *)a.err : 0)) return;
     const int N = pr.N, ldp = pr.ldp;
     const int i0 = it.z * kR, cs = it.w, k0 = cs * S;
-    const int Wc = min(S, N - k0);
     const int64_t base = pr.off + (int64_t)it.y * pr.rhs;
     const T *src = (MODE == 0 ? a.rho0 : a.cl) + base;
     T *Dp = a.D + base;
@@ -200,12 +213,12 @@ __global__ void __launch_bounds__(kR) row_pass_kernel(SwArgs<T> a, int j)
     const int sc = i0 / S, segstart = sc * S, segend = min(segstart + S, N);
     const int s_above = (MODE > 0 && i0 == segstart && i0 > 0) ? sc - 1 : -1;
     const int s_below = (MODE > 0 && i0 + kR == segend && segend < N) ? sc + 1 : -1;
-    const int rows_ld = MODE == 0 ? kR : kR + 4;
-    const int row0 = MODE == 0 ? i0 : i0 - 2;   // first global row loaded
-    const int smr0 = MODE == 0 ? 2 : 0;          // its shared-memory row
-    const int cw = MODE == 0 ? Wc : Wc + 8;      // loaded columns
-    const int kc0 = MODE == 0 ? k0 : k0 - 4;     // first loaded column
-    const int scc0 = MODE == 0 ? 4 : 0;          // its shared-memory column
+    constexpr int rows_ld = MODE == 0 ? kR : kR + 4;
+    constexpr int cw = MODE == 0 ? W : W + 8;  // loaded columns
+    const int row0 = MODE == 0 ? i0 : i0 - 2;  // first global row loaded
+    constexpr int smr0 = MODE == 0 ? 2 : 0;    // its shared-memory row
+    const int kc0 = MODE == 0 ? k0 : k0 - 4;   // first loaded column
+    constexpr int scc0 = MODE == 0 ? 4 : 0;    // its shared-memory column
 
     if (tid == 0) {
         bulk::mbar_init(bar, 1);
@@ -213,54 +226,67 @@ __global__ void __launch_bounds__(kR) row_pass_kernel(SwArgs<T> a, int j)
     }
     __syncthreads();
     if (tid == 0) {
-        unsigned bytes = (unsigned)(rows_ld * cw * sizeof(T) + Wc * sizeof(Fac<T>));
+        unsigned bytes = (unsigned)(rows_ld * cw * sizeof(T) + W * sizeof(Fac<T>));
         if (MODE > 0)
             bytes += (unsigned)((kR + 4) * sizeof(Fac<T>) +
                                 2 * cw * sizeof(T2) * (1 + (s_above >= 0) + (s_below >= 0)));
         bulk::mbar_arrive_expect_tx(bar, bytes);
     }
     __syncthreads();
-    for (int r = tid; r < rows_ld; r += kR)
+    for (int r = tid; r < rows_ld; r += kRT)
         bulk::g2s(ct + (smr0 + r) * SW + scc0, src + (int64_t)(row0 + r + 2) * ldp + (kc0 + 4),
                   (unsigned)(cw * sizeof(T)), bar);
-    if (tid == kR - 1) bulk::g2s(fcol, facj + k0 + 2, (unsigned)(Wc * sizeof(Fac<T>)), bar);
+    if (tid == kRT - 1) bulk::g2s(fcol, facj + k0 + 2, (unsigned)(W * sizeof(Fac<T>)), bar);
     if (MODE > 0) {
-        if (tid == kR - 2) bulk::g2s(frow, facp + i0, (unsigned)((kR + 4) * sizeof(Fac<T>)), bar);
-        if (tid >= kR - 8 && tid < kR - 2) {
-            const int k = tid - (kR - 8), slot = k >> 1, par = k & 1;
+        if (tid == kRT - 2) bulk::g2s(frow, facp + i0, (unsigned)((kR + 4) * sizeof(Fac<T>)), bar);
+        if (tid >= kRT - 8 && tid < kRT - 2) {
+            const int k = tid - (kRT - 8), slot = k >> 1, par = k & 1;
             const int sg = slot == 0 ? s_above : (slot == 1 ? sc : s_below);
             if (sg >= 0)
                 bulk::g2s(zx + (slot * 2 + par) * (S + 8), a.zxC + sbase + ((int64_t)sg * 2 + par) * (N + 8) + k0,
                           (unsigned)(cw * sizeof(T2)), bar);
         }
-        bulk::prefetch_l2(Dp + (int64_t)(i0 + tid + 2) * ldp + (k0 + 4), (unsigned)(Wc * sizeof(T)));
+    }
+    // D of the tile's core into registers while the tile is in flight: thread t owns
+    // chunk t % CPR of rows t / CPR + m * (kRT / CPR) (coalesced 16-byte loads)
+    constexpr int CPR = W / V;
+    constexpr int DSTEP = kRT / CPR;
+    constexpr int NDC = kR / DSTEP;  // chunks per thread
+    const int dr0 = tid / CPR, dc = tid % CPR;
+    T dreg[NDC][V];
+    if (MODE == 2) {
+#pragma unroll
+        for (int m = 0; m < NDC; ++m)
+            ld16(Dp + (int64_t)(i0 + dr0 + m * DSTEP + 2) * ldp + (k0 + 4 + dc * V), dreg[m]);
     }
     if (!tile_ready(bar, a.err)) return;
 
-    // ip-scaled row-stencil coefficients of this tile's columns
-    for (int c = tid; c < Wc; c += kR) {
+    // per-column records {ip e_{k-2}, ip (d_k + q), ip e_k, g} of the ip-scaled row stencil
+    for (int c = tid; c < W; c += kRT) {
         const int k = k0 + c;
         const T ipk = fcol[c].ip;
         if (MODE > 0) {
-            cA[c] = ipk * pr.e[k];               // e_{k-2}
-            cB[c] = ipk * (pr.d[k + 2] + qprev);
-            cC[c] = ipk * pr.e[k + 2];           // e_k
+            cf[4 * c + 0] = ipk * pr.e[k];
+            cf[4 * c + 1] = ipk * (pr.d[k + 2] + qprev);
+            cf[4 * c + 2] = ipk * pr.e[k + 2];
         } else {
-            cB[c] = ipk;
+            cf[4 * c + 0] = T(0);
+            cf[4 * c + 1] = ipk;
+            cf[4 * c + 2] = T(0);
         }
+        cf[4 * c + 3] = fcol[c].g;
     }
     if (MODE > 0) {
-        // rebuild c_{j-1} = cl + Bv zin + Psi xout on the whole loaded tile; D update on its core
-        const T q2 = T(2) * qprev;
-        const int cpr = cw / V;
-        const int total = (kR + 4) * cpr;
-        for (int idx = tid; idx < total; idx += kR) {
+        // rebuild c_{j-1} = cl + Bv zin + Psi xout on the whole loaded tile
+        constexpr int cpr = cw / V;
+        constexpr int total = (kR + 4) * cpr;
+        for (int idx = tid; idx < total; idx += kRT) {
             const int r = idx / cpr, cc = (idx - r * cpr) * V;
             const int i = i0 - 2 + r;
-            T *cp = ct + r * SW + cc;
-            T v[V];
-            ld16(cp, v);
             if (i >= 0 && i < N) {
+                T *cp = ct + r * SW + cc;
+                T v[V];
+                ld16(cp, v);
                 const int slot = i < segstart ? 0 : (i >= segend ? 2 : 1);
                 const T2 *z = zx + (slot * 2 + (i & 1)) * (S + 8) + cc;
                 const T bv = frow[r].Bv, ps = frow[r].Psi;
@@ -270,163 +296,112 @@ __global__ void __launch_bounds__(kR) row_pass_kernel(SwArgs<T> a, int j)
                     v[e] = fma(bv, zz.x, fma(ps, zz.y, v[e]));
                 }
                 st16(cp, v);
-                if (r >= 2 && r < kR + 2 && cc >= 4 && cc < Wc + 4) {
-                    T *dp = Dp + (int64_t)(i + 2) * ldp + (k0 + cc);
-                    T dv[V];
-                    if (MODE == 1) {
-#pragma unroll
-                        for (int e = 0; e < V; ++e) dv[e] = -q2 * v[e];
-                    } else {
-                        ld16(dp, dv);
-#pragma unroll
-                        for (int e = 0; e < V; ++e) dv[e] = fma(-q2, v[e], dv[e]);
-                    }
-                    st16(dp, dv);
-                }
             }
+        }
+        __syncthreads();
+        // D -= 2 q_{j-1} c_{j-1} on the core (D = -2 q_0 c_0 at j = 1)
+        const T q2 = T(2) * qprev;
+#pragma unroll
+        for (int m = 0; m < NDC; ++m) {
+            const int rr = dr0 + m * DSTEP;
+            T v[V], dv[V];
+            ld16(ct + (rr + 2) * SW + 4 + dc * V, v);
+#pragma unroll
+            for (int e = 0; e < V; ++e) dv[e] = MODE == 1 ? -q2 * v[e] : fma(-q2, v[e], dreg[m][e]);
+            st16(Dp + (int64_t)(i0 + rr + 2) * ldp + (k0 + 4 + dc * V), dv);
         }
     }
     __syncthreads();
 
-    // one thread per row: rho' = ip * (R + q)(L + q) c (or ip * rho_0), forward sweep
-    const int r = tid + 2;
-    const int i = i0 + tid;
-    T wr[S];
-    T we0 = 0, we1 = 0;
+    // one thread per (row, parity of the column index): a warp holds 16 rows x 2 parities
+    const int lane = tid & 31;
+    const int rr = (tid >> 5) * 16 + (lane & 15), p = lane >> 4;
+    const int r = rr + 2, i = i0 + rr;
+    T wr[W / 2];
+    T we;
     {
-        T w0 = 0, w1 = 0;
+        T w = 0;
         if (MODE == 0) {
 #pragma unroll
-            for (int m = 0; m < S / V; ++m) {
-                if (m * V < Wc) {
-                    T v[V], b[V];
-                    ld16(ct + r * SW + 4 + m * V, v);
-                    ld16(cB + m * V, b);
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const int c = m * V + e;
-                        const T g = fcol[c].g;
-                        if (e & 1) {
-                            w1 = fma(-g, w1, b[e] * v[e]);
-                            wr[c] = w1;
-                        } else {
-                            w0 = fma(-g, w0, b[e] * v[e]);
-                            wr[c] = w0;
-                        }
-                        if (c == Wc - 2) we0 = w0;
-                        if (c == Wc - 1) we1 = w1;
-                    }
-                }
+            for (int t = 0; t < W / 2; ++t) {
+                const int c = 2 * t + p;
+                const T rho = cf[4 * c + 1] * ct[r * SW + 4 + c];
+                w = fma(-cf[4 * c + 3], w, rho);
+                wr[t] = w;
             }
         } else {
+            // rho = ip (R + q)(L + q) c: column stencil u = (L + q) c, then the row stencil
             const T eu = pr.e[i], dq = pr.d[i + 2] + qprev, ed = pr.e[i + 2];
-            const T *r0 = ct + (r - 2) * SW, *r1 = ct + r * SW, *r2 = ct + (r + 2) * SW;
-            // window of column-stencil values u = (L + q) c over three chunks
-            T U[3 * V];
-            auto ucol = [&](int q, T *dst) {
-                T x0[V], x1[V], x2[V];
-                ld16(r0 + q * V, x0);
-                ld16(r1 + q * V, x1);
-                ld16(r2 + q * V, x2);
+            const T *r0 = ct + (r - 2) * SW + 4, *r1 = ct + r * SW + 4, *r2 = ct + (r + 2) * SW + 4;
+            auto u = [&](int x) { return fma(eu, r0[x], fma(dq, r1[x], ed * r2[x])); };
+            T um = u(p - 2), u0 = u(p);
 #pragma unroll
-                for (int e = 0; e < V; ++e) dst[e] = fma(eu, x0[e], fma(dq, x1[e], ed * x2[e]));
-            };
-            constexpr int q0 = 4 / V;  // chunk of shared column 4 (local column 0)
-            ucol(q0 - 1, U);
-            ucol(q0, U + V);
-#pragma unroll
-            for (int m = 0; m < S / V; ++m) {
-                if (m * V < Wc) {
-                    const int q = q0 + m;
-                    ucol(q + 1, U + 2 * V);
-                    T ca[V], cb[V], cc[V];
-                    ld16(cA + m * V, ca);
-                    ld16(cB + m * V, cb);
-                    ld16(cC + m * V, cc);
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const int c = m * V + e;
-                        const T rho = fma(ca[e], U[V + e - 2], fma(cb[e], U[V + e], cc[e] * U[V + e + 2]));
-                        const T g = fcol[c].g;
-                        if (e & 1) {
-                            w1 = fma(-g, w1, rho);
-                            wr[c] = w1;
-                        } else {
-                            w0 = fma(-g, w0, rho);
-                            wr[c] = w0;
-                        }
-                        if (c == Wc - 2) we0 = w0;
-                        if (c == Wc - 1) we1 = w1;
-                    }
-#pragma unroll
-                    for (int e = 0; e < 2 * V; ++e) U[e] = U[e + V];
-                }
+            for (int t = 0; t < W / 2; ++t) {
+                const int c = 2 * t + p;
+                const T up = u(c + 2);
+                T cA, cB, cC, g;
+                ld4(cf + 4 * c, cA, cB, cC, g);
+                const T rho = fma(cA, um, fma(cB, u0, cC * up));
+                w = fma(-g, w, rho);
+                wr[t] = w;
+                um = u0;
+                u0 = up;
             }
         }
+        we = w;
     }
-    // back substitution (local: zero beyond the segment)
     {
-        T x0 = 0, x1 = 0;
+        T x = 0;  // local back substitution: zero beyond the segment
 #pragma unroll
-        for (int c = S - 1; c >= 0; --c) {
-            if (c < Wc) {
-                const T uf = fcol[c].uf;
-                if (c & 1) {
-                    x1 = fma(-uf, x1, wr[c]);
-                    wr[c] = x1;
-                } else {
-                    x0 = fma(-uf, x0, wr[c]);
-                    wr[c] = x0;
-                }
-            }
+        for (int t = W / 2 - 1; t >= 0; --t) {
+            x = fma(-fcol[2 * t + p].uf, x, wr[t]);
+            wr[t] = x;
         }
     }
     const bool live = i < pr.n;
     __syncthreads();  // every thread is done reading the tile
 #pragma unroll
-    for (int m = 0; m < S / V; ++m) {
-        if (m * V < Wc) {
-            T v[V];
-#pragma unroll
-            for (int e = 0; e < V; ++e) v[e] = live ? wr[m * V + e] : T(0);
-            st16(ct + r * SW + 4 + m * V, v);
-        }
-    }
-    {
-        typename Vec2<T>::type *sm = a.sumR + sbase;
-        sm[((int64_t)cs * 2 + 0) * (N + 8) + i + 4] = mk2<T>(live ? we0 : T(0), live ? wr[0] : T(0));
-        sm[((int64_t)cs * 2 + 1) * (N + 8) + i + 4] = mk2<T>(live ? we1 : T(0), live ? wr[1] : T(0));
-    }
+    for (int t = 0; t < W / 2; ++t) ct[r * SW + 4 + 2 * t + p] = live ? wr[t] : T(0);
+    a.sumR[sbase + ((int64_t)cs * 2 + p) * (N + 8) + i + 4] = mk2<T>(live ? we : T(0), live ? wr[0] : T(0));
     bulk::fence_proxy_async_shared();
     __syncthreads();
-    bulk::s2g(alp + (int64_t)(i + 2) * ldp + (k0 + 4), ct + r * SW + 4, (unsigned)(Wc * sizeof(T)));
+    if (tid < kR)
+        bulk::s2g(alp + (int64_t)(i0 + tid + 2) * ldp + (k0 + 4), ct + (tid + 2) * SW + 4, (unsigned)(W * sizeof(T)));
     bulk::commit();
     bulk::wait_read_all();
 }
 
+template <typename T, int S, int MODE>
+__global__ void __launch_bounds__(kRT, 3) row_pass_kernel(SwArgs<T> a, int j)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int4 it = a.items[blockIdx.x];
+    const SwProb<T> &pr = a.probs[it.x];
+    if (!a.active[it.x] || j >= pr.J) return;
+    // after a timeout anywhere, leave at once (one read, agreed on by the whole CTA)
+    if (__syncthreads_or(threadIdx.x == 0 ? *(volatile int *)a.err : 0)) return;
+    if (S == kR || pr.N - it.w * S >= S) row_pass_tile<T, S, MODE, S>(a, j, it, pr, smem);
+    else row_pass_tile<T, S, MODE, kR>(a, j, it, pr, smem);
+}
+
 // ---------------------------------------------------------------------------
 // Column pass.  Item {problem, rhs, column block (64 columns), row segment}.
+// H: rows of this tile's segment (S, or 64 for a short last segment).
 // ---------------------------------------------------------------------------
-template <typename T, int S>
-__global__ void __launch_bounds__(kC) col_pass_kernel(SwArgs<T> a, int j)
+template <typename T, int S, int H>
+__device__ __forceinline__ void col_pass_tile(const SwArgs<T> &a, int j, const int4 it, const SwProb<T> &pr,
+                                              unsigned char *smem)
 {
     using G = ColGeom<T, S>;
     using T2 = typename Vec2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     T *tile = reinterpret_cast<T *>(smem + G::off_tile);
     Fac<T> *fac = reinterpret_cast<Fac<T> *>(smem + G::off_fac);
     T2 *zx = reinterpret_cast<T2 *>(smem + G::off_zx);
 
-    const int4 it = a.items[blockIdx.x];
-    const SwProb<T> &pr = a.probs[it.x];
-    if (!a.active[it.x] || j >= pr.J) return;
     const int tid = threadIdx.x;
-    // after a timeout anywhere, leave at once (one read, agreed on by the whole CTA)
-    if (__syncthreads_or(tid == 0 ? *(volatile int *)a.err : 0)) return;
     const int N = pr.N, ldp = pr.ldp;
     const int k0 = it.z * kC, rs = it.w, i0 = rs * S;
-    const int Hr = min(S, N - i0);
     const int cs = k0 / S;  // row-system segment holding these columns
     const int64_t base = pr.off + (int64_t)it.y * pr.rhs;
     const int64_t sbase = pr.soff + (int64_t)it.y * pr.srhs;
@@ -438,79 +413,70 @@ __global__ void __launch_bounds__(kC) col_pass_kernel(SwArgs<T> a, int j)
     }
     __syncthreads();
     if (tid == 0)
-        bulk::mbar_arrive_expect_tx(bar, (unsigned)(Hr * kC * sizeof(T) + Hr * sizeof(Fac<T>) + 2 * Hr * sizeof(T2)));
+        bulk::mbar_arrive_expect_tx(bar, (unsigned)(H * kC * sizeof(T) + H * sizeof(Fac<T>) + 2 * H * sizeof(T2)));
     __syncthreads();
-    for (int r = tid; r < Hr; r += kC)
+    for (int r = tid; r < H; r += kCT)
         bulk::g2s(tile + r * kC, a.al + base + (int64_t)(i0 + r + 2) * ldp + (k0 + 4), (unsigned)(kC * sizeof(T)), bar);
-    if (tid == kC - 1) bulk::g2s(fac, facj + i0 + 2, (unsigned)(Hr * sizeof(Fac<T>)), bar);
-    if (tid == kC - 2 || tid == kC - 3) {
-        const int par = kC - 2 - tid;
+    if (tid == kCT - 1) bulk::g2s(fac, facj + i0 + 2, (unsigned)(H * sizeof(Fac<T>)), bar);
+    if (tid == kCT - 2 || tid == kCT - 3) {
+        const int par = kCT - 2 - tid;
         bulk::g2s(zx + par * G::ZS, a.zxR + sbase + ((int64_t)cs * 2 + par) * (N + 8) + i0 + 4,
-                  (unsigned)(Hr * sizeof(T2)), bar);
+                  (unsigned)(H * sizeof(T2)), bar);
     }
-    const int k = k0 + tid;
-    const Fac<T> fk = facj[k + 2];
+    // one thread per (column, parity of the row index)
+    const int kk = tid % kC, p = tid / kC;
+    const int k = k0 + kk;
+    const T bv = facj[k + 2].Bv, ps = facj[k + 2].Psi;
     const T2 *zp = zx + (k & 1) * G::ZS;
     if (!tile_ready(bar, a.err)) return;
 
-    T wr[S];
-    T we0 = 0, we1 = 0;
-    {
-        T w0 = 0, w1 = 0;
-#pragma unroll
-        for (int r = 0; r < S; ++r) {
-            if (r < Hr) {
-                const T2 z = zp[r];
-                const T av = fma(fk.Bv, z.x, fma(fk.Psi, z.y, tile[r * kC + tid]));
-                const T ip = fac[r].ip, g = fac[r].g;
-                if (r & 1) {
-                    w1 = fma(-g, w1, ip * av);
-                    wr[r] = w1;
-                } else {
-                    w0 = fma(-g, w0, ip * av);
-                    wr[r] = w0;
-                }
-                if (r == Hr - 2) we0 = w0;
-                if (r == Hr - 1) we1 = w1;
-            }
-        }
-    }
-    {
-        T x0 = 0, x1 = 0;
-#pragma unroll
-        for (int r = S - 1; r >= 0; --r) {
-            if (r < Hr) {
-                const T uf = fac[r].uf;
-                if (r & 1) {
-                    x1 = fma(-uf, x1, wr[r]);
-                    wr[r] = x1;
-                } else {
-                    x0 = fma(-uf, x0, wr[r]);
-                    wr[r] = x0;
-                }
-            }
-        }
-    }
+    // forward sweep and back substitution in place in the tile (own column, own parity)
     const bool live = k < pr.n;
-#pragma unroll
-    for (int r = 0; r < S; ++r)
-        if (r < Hr) tile[r * kC + tid] = live ? wr[r] : T(0);
+    T we, x = 0;
     {
-        T2 *sm = a.sumC + sbase;
-        sm[((int64_t)rs * 2 + 0) * (N + 8) + k + 4] = mk2<T>(live ? we0 : T(0), live ? wr[0] : T(0));
-        sm[((int64_t)rs * 2 + 1) * (N + 8) + k + 4] = mk2<T>(live ? we1 : T(0), live ? wr[1] : T(0));
+        T w = 0;
+#pragma unroll 8
+        for (int t = 0; t < H / 2; ++t) {
+            const int r = 2 * t + p;
+            const T2 z = zp[r];
+            const T av = fma(bv, z.x, fma(ps, z.y, tile[r * kC + kk]));
+            T ip, g, uf, phi;
+            ld4(&fac[r].ip, ip, g, uf, phi);
+            w = fma(-g, w, ip * av);
+            tile[r * kC + kk] = w;
+        }
+        we = w;
     }
+#pragma unroll 8
+    for (int t = H / 2 - 1; t >= 0; --t) {
+        const int r = 2 * t + p;
+        x = fma(-fac[r].uf, x, tile[r * kC + kk]);
+        tile[r * kC + kk] = live ? x : T(0);
+    }
+    a.sumC[sbase + ((int64_t)rs * 2 + p) * (N + 8) + k + 4] = mk2<T>(live ? we : T(0), live ? x : T(0));
     bulk::fence_proxy_async_shared();
     __syncthreads();
-    for (int r = tid; r < Hr; r += kC)
+    for (int r = tid; r < H; r += kCT)
         bulk::s2g(a.cl + base + (int64_t)(i0 + r + 2) * ldp + (k0 + 4), tile + r * kC, (unsigned)(kC * sizeof(T)));
     bulk::commit();
     bulk::wait_read_all();
 }
 
+template <typename T, int S>
+__global__ void __launch_bounds__(kCT) col_pass_kernel(SwArgs<T> a, int j)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int4 it = a.items[blockIdx.x];
+    const SwProb<T> &pr = a.probs[it.x];
+    if (!a.active[it.x] || j >= pr.J) return;
+    if (__syncthreads_or(threadIdx.x == 0 ? *(volatile int *)a.err : 0)) return;
+    if (S == kC || pr.N - it.w * S >= S) col_pass_tile<T, S, S>(a, j, it, pr, smem);
+    else col_pass_tile<T, S, kC>(a, j, it, pr, smem);
+}
+
 // ---------------------------------------------------------------------------
 // Chains: true forward value entering and true solution leaving every segment.
-// Item {problem, rhs, block of 128 lines}; thread = (line, parity).
+// Item {problem, rhs, block of 64 lines}; thread = (line, parity).
 //   W_s = wl_end(s) + phi_end(s) W_{s-1},           zin(s)  = W_{s-1}
 //   X_s = xl_start(s) + Bv_start(s) zin(s) + Psi_start(s) X_{s+1},   xout(s) = X_{s+1}
 // ---------------------------------------------------------------------------
@@ -518,6 +484,7 @@ template <typename T>
 __global__ void __launch_bounds__(2 * kChainLines) chain_kernel(SwArgs<T> a, int dir, int j)
 {
     using T2 = typename Vec2<T>::type;
+    constexpr int B = 16;  // segments whose loads are issued together
     const int4 it = a.items[blockIdx.x];
     const SwProb<T> &pr = a.probs[it.x];
     if (!a.active[it.x] || j >= pr.J) return;
@@ -526,28 +493,52 @@ __global__ void __launch_bounds__(2 * kChainLines) chain_kernel(SwArgs<T> a, int
     const int N = pr.N, S = pr.S, P = pr.P;
     if (l >= N) return;
     const int64_t sbase = pr.soff + (int64_t)it.y * pr.srhs;
-    const T2 *sum = (dir == 0 ? a.sumR : a.sumC) + sbase;
-    T2 *zx = (dir == 0 ? a.zxR : a.zxC) + sbase;
-    T *zs = a.zin + sbase;
-    const Fac<T> *facj = pr.fac + (int64_t)j * (N + 4) + 2;
+    const T2 *__restrict__ sum = (dir == 0 ? a.sumR : a.sumC) + sbase + p * (N + 8) + l + 4;
+    T2 *__restrict__ zx = (dir == 0 ? a.zxR : a.zxC) + sbase + p * (N + 8) + l + 4;
+    T *__restrict__ zs = a.zin + sbase + p * (N + 8) + l + 4;
+    const int64_t step = 2 * (int64_t)(N + 8);  // next segment, same parity and line
+    const Fac<T> *__restrict__ facj = pr.fac + (int64_t)j * (N + 4) + 2;
     T W = 0;
-#pragma unroll 4
-    for (int s = 0; s < P; ++s) {
-        const int64_t idx = ((int64_t)s * 2 + p) * (N + 8) + l + 4;
-        const T2 sm = sum[idx];
-        const int pe = min(s * S + S, N) - 2 + p;
-        zs[idx] = W;
-        W = fma(facj[pe].phi, W, sm.x);
+    for (int s0 = 0; s0 < P; s0 += B) {
+        T sx[B], ph[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int s = s0 + b;
+            if (s < P) {
+                sx[b] = sum[s * step].x;
+                ph[b] = facj[min(s * S + S, N) - 2 + p].phi;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int s = s0 + b;
+            if (s < P) {
+                zs[s * step] = W;
+                W = fma(ph[b], W, sx[b]);
+            }
+        }
     }
     T X = 0;
-#pragma unroll 4
-    for (int s = P - 1; s >= 0; --s) {
-        const int64_t idx = ((int64_t)s * 2 + p) * (N + 8) + l + 4;
-        const T2 sm = sum[idx];
-        const T zi = zs[idx];
-        const Fac<T> fb = facj[s * S + p];
-        zx[idx] = mk2<T>(zi, X);
-        X = fma(fb.Bv, zi, fma(fb.Psi, X, sm.y));
+    for (int s1 = P - 1; s1 >= 0; s1 -= B) {
+        T sy[B], zi[B], bv[B], ps[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int s = s1 - b;
+            if (s >= 0) {
+                sy[b] = sum[s * step].y;
+                zi[b] = zs[s * step];
+                bv[b] = facj[s * S + p].Bv;
+                ps[b] = facj[s * S + p].Psi;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int s = s1 - b;
+            if (s >= 0) {
+                zx[s * step] = mk2<T>(zi[b], X);
+                X = fma(bv[b], zi[b], fma(ps[b], X, sy[b]));
+            }
+        }
     }
 }
 
@@ -744,20 +735,26 @@ __global__ void __launch_bounds__(256) scale_out_kernel(TileArgs t, const double
     }
 }
 
-template <typename T>
-struct SegLen;
-template <>
-struct SegLen<float> {
-    static constexpr int S = 128;
-};
-template <>
-struct SegLen<double> {
-    static constexpr int S = 64;
-};
+template <typename T, int S>
+cudaError_t row_pass_S(const SwArgs<T> &a, int j, int mode, cudaStream_t st)
+{
+    const size_t sm = RowGeom<T, S>::bytes;
+    const dim3 grid((unsigned)a.nitems);
+    if (mode == 0) row_pass_kernel<T, S, 0><<<grid, kRT, sm, st>>>(a, j);
+    else if (mode == 1) row_pass_kernel<T, S, 1><<<grid, kRT, sm, st>>>(a, j);
+    else row_pass_kernel<T, S, 2><<<grid, kRT, sm, st>>>(a, j);
+    return cudaGetLastError();
+}
+template <typename T, int S>
+cudaError_t col_pass_S(const SwArgs<T> &a, int j, cudaStream_t st)
+{
+    col_pass_kernel<T, S><<<(unsigned)a.nitems, kCT, ColGeom<T, S>::bytes, st>>>(a, j);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
-int sweep_segment_length(bool fp64) { return fp64 ? SegLen<double>::S : SegLen<float>::S; }
+bool sweep_segment_supported(bool fp64, int S) { return S == 64 || (!fp64 && S == 128); }
 
 cudaError_t sweep_setup_kernels()
 {
@@ -769,10 +766,14 @@ cudaError_t sweep_setup_kernels()
     SETSM((row_pass_kernel<float, 128, 0>), (RowGeom<float, 128>::bytes));
     SETSM((row_pass_kernel<float, 128, 1>), (RowGeom<float, 128>::bytes));
     SETSM((row_pass_kernel<float, 128, 2>), (RowGeom<float, 128>::bytes));
+    SETSM((row_pass_kernel<float, 64, 0>), (RowGeom<float, 64>::bytes));
+    SETSM((row_pass_kernel<float, 64, 1>), (RowGeom<float, 64>::bytes));
+    SETSM((row_pass_kernel<float, 64, 2>), (RowGeom<float, 64>::bytes));
     SETSM((row_pass_kernel<double, 64, 0>), (RowGeom<double, 64>::bytes));
     SETSM((row_pass_kernel<double, 64, 1>), (RowGeom<double, 64>::bytes));
     SETSM((row_pass_kernel<double, 64, 2>), (RowGeom<double, 64>::bytes));
     SETSM((col_pass_kernel<float, 128>), (ColGeom<float, 128>::bytes));
+    SETSM((col_pass_kernel<float, 64>), (ColGeom<float, 64>::bytes));
     SETSM((col_pass_kernel<double, 64>), (ColGeom<double, 64>::bytes));
 #undef SETSM
     return cudaSuccess;
@@ -789,21 +790,21 @@ cudaError_t launch_fac_tables(const FacJob<T> *jobs, int njobs, cudaStream_t st)
 template <typename T>
 cudaError_t launch_row_pass(const SwArgs<T> &a, int j, int mode, cudaStream_t st)
 {
-    constexpr int S = SegLen<T>::S;
-    const size_t sm = RowGeom<T, S>::bytes;
-    const dim3 grid((unsigned)a.nitems);
-    if (mode == 0) row_pass_kernel<T, S, 0><<<grid, kR, sm, st>>>(a, j);
-    else if (mode == 1) row_pass_kernel<T, S, 1><<<grid, kR, sm, st>>>(a, j);
-    else row_pass_kernel<T, S, 2><<<grid, kR, sm, st>>>(a, j);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+        if (a.S == 128) return row_pass_S<T, 128>(a, j, mode, st);
+    }
+    if (a.S == 64) return row_pass_S<T, 64>(a, j, mode, st);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t launch_col_pass(const SwArgs<T> &a, int j, cudaStream_t st)
 {
-    constexpr int S = SegLen<T>::S;
-    col_pass_kernel<T, S><<<(unsigned)a.nitems, kC, ColGeom<T, S>::bytes, st>>>(a, j);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+        if (a.S == 128) return col_pass_S<T, 128>(a, j, st);
+    }
+    if (a.S == 64) return col_pass_S<T, 64>(a, j, st);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

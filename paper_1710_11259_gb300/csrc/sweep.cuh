@@ -54,10 +54,11 @@ struct Vec2<double> {
 // Per-position coefficients of one shift (position i at index i + 2 of a table of
 // N + 4 records; the two records on each side and positions >= n are zero).
 template <typename T>
-struct Fac {
+struct alignas(16) Fac {
     T ip, g, uf;   // pivot reciprocal, forward multiplier, back-substitution multiplier
     T phi;         // prod of -g from the segment start to i (forward propagation of zin)
     T Bv, Psi;     // coefficients of zin and xout in the true solution at i
+    T pad0, pad1;  // 8-word records: the first four words load as 16-byte vectors
 };
 
 // One problem at one tolerance level (device table entry).
@@ -76,7 +77,7 @@ struct SwArgs {
     using T2 = typename Vec2<T>::type;
     const SwProb<T> *probs;
     const int4 *items;     // row/column pass: {problem, rhs, block of 64 rows/columns, segment}
-                           // chain: {problem, rhs, block of 128 lines, 0}
+                           // chain: {problem, rhs, block of 64 lines, 0}
     int64_t nitems;
     const int *active;     // per problem
     T *rho0, *cl, *al, *D;
@@ -84,6 +85,7 @@ struct SwArgs {
     T2 *zxR, *zxC;         // chain results {zin, xout}
     T *zin;                // chain scratch ([P][2][N + 8] per rhs)
     int *err;              // device error word: bit 0 = a bounded wait gave up
+    int S;                 // segment length of every problem (sweep_segment_supported)
 };
 
 // Elementwise tile kernels of the solve around the ADI loop.  A tile item is
@@ -94,10 +96,6 @@ struct TileProb {
     int64_t off, rhs;       // padded T arrays (as SwProb)
     const double *d, *e, *s;  // FP64 bands of A~ (d, e zero-padded to length n) and 1/sqrt(E)
     int pair0;              // index of (problem, rhs 0) among all pairs
-    int J;                  // iterations of the level last run (finalize)
-    const void *fac;        // Fac<T> table of that level ([J][N + 4])
-    const void *q;          // T shifts of that level
-    int S;
 };
 
 struct TileArgs {
@@ -116,6 +114,8 @@ struct FacJob {
 };
 
 cudaError_t sweep_setup_kernels();
+// Segment lengths with compiled pass kernels: 64 (FP32, FP64) and 128 (FP32).
+bool sweep_segment_supported(bool fp64, int S);
 
 template <typename T>
 cudaError_t launch_fac_tables(const FacJob<T> *jobs, int njobs, cudaStream_t st);

@@ -20,14 +20,17 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
+
+#include <sys/stat.h>
 
 #include "../../include/fps.h"
 #include "host_math.h"
 
 namespace fps {
-
-int sweep_segment_length(bool fp64);
 
 namespace {
 double bits_to_double(unsigned long long b)
@@ -38,7 +41,7 @@ double bits_to_double(unsigned long long b)
 }
 const double kLevelTols[] = {1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2};
 constexpr int kTileW = 64;       // rows of a row-pass tile / columns of a column-pass tile
-constexpr int kChainLines = 128;
+constexpr int kChainLines = 64;
 }  // namespace
 
 template <typename T>
@@ -80,9 +83,111 @@ void SweepEngine<T>::release()
         }                                                                                                \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// Autotuner of the segment length (the tile height of the column pass and width of
+// the row pass; it also fixes the number of segments a chain walks).  Every
+// candidate gets a complete engine of its own on the same sizes; the graph of the
+// coarsest tolerance level is timed with CUDA events and the fastest candidate
+// kept.  Results are cached per (GPU name, nrhs, size list) in $FPS_AUTOTUNE_CACHE
+// (default ~/.cache/fps_gb300_autotune.txt); FPS_AUTOTUNE=0 skips tuning (128).
+// ---------------------------------------------------------------------------
+namespace {
+std::string tune_key(const std::vector<int64_t> &ns, int nrhs)
+{
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    uint64_t h = 1469598103934665603ULL;  // FNV-1a over the sizes
+    for (int64_t n : ns) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (uint64_t)((n >> (8 * b)) & 0xff);
+            h *= 1099511628211ULL;
+        }
+    }
+    std::ostringstream os;
+    os << "seg|" << name << "|" << nrhs << "|" << ns.size() << "|" << std::hex << h;
+    return os.str();
+}
+
+std::string tune_cache_path()
+{
+    const char *p = std::getenv("FPS_AUTOTUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = std::getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/fps_gb300_autotune.txt";
+}
+}  // namespace
+
+template <typename T>
+int SweepEngine<T>::time_level(size_t li, int reps, float &ms, std::string &err)
+{
+    cudaEvent_t e0, e1;
+    ENG_CK(cudaEventCreate(&e0));
+    ENG_CK(cudaEventCreate(&e1));
+    ENG_CK(cudaGraphLaunch(levels_[li].graph, cap_));  // warm-up
+    ENG_CK(cudaEventRecord(e0, cap_));
+    for (int r = 0; r < reps; ++r) ENG_CK(cudaGraphLaunch(levels_[li].graph, cap_));
+    ENG_CK(cudaEventRecord(e1, cap_));
+    ENG_CK(cudaEventSynchronize(e1));
+    ENG_CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ms /= (float)reps;
+    return FPS_OK;
+}
+
+template <typename T>
+int SweepEngine<T>::autotune(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight, std::string &err)
+{
+    seg_len = 128;
+    const char *env = std::getenv("FPS_AUTOTUNE");
+    if (env && std::string(env) == "0") return FPS_OK;
+    const std::string key = tune_key(ns, nrhs);
+    const std::string path = tune_cache_path();
+    {
+        std::ifstream in(path);
+        std::string k;
+        int v;
+        while (in >> k >> v)
+            if (k == key && sweep_segment_supported(false, v)) {
+                seg_len = v;
+                return FPS_OK;
+            }
+    }
+    const int cand[] = {64, 128};
+    float best = 3.4e38f;
+    tune_ms.clear();
+    for (int S : cand) {
+        SweepEngine<T> t;
+        std::string e2;
+        int st = t.create(ns, nrhs, tol, tight, cap_, e2, S);
+        float ms = 0.f;
+        if (st == FPS_OK) st = t.time_level(t.levels_.size() - 1, 2, ms, e2);
+        t.release();
+        if (st != FPS_OK) {
+            err = "autotune: " + e2;
+            return st;
+        }
+        tune_ms.push_back(ms);
+        if (ms < best) {
+            best = ms;
+            seg_len = S;
+        }
+    }
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // may exist
+    std::ofstream out(path, std::ios::app);
+    if (out) out << key << " " << seg_len << "\n";
+    return FPS_OK;
+}
+
 template <typename T>
 int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight,
-                           cudaStream_t setup_stream, std::string &err)
+                           cudaStream_t setup_stream, std::string &err, int seg)
 {
     constexpr bool kFP64 = sizeof(T) == 8;
     ns_ = ns;
@@ -90,7 +195,21 @@ int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol,
     tol_ = tol;
     cap_ = setup_stream;
     const int np = (int)ns.size();
-    const int S = sweep_segment_length(kFP64);
+    if (seg <= 0) {
+        if (kFP64) {
+            seg_len = 64;
+        } else {
+            const int st = autotune(ns, nrhs, tol, tight, err);
+            if (st != FPS_OK) return st;
+        }
+    } else {
+        if (!sweep_segment_supported(kFP64, seg)) {
+            err = "unsupported segment length";
+            return FPS_ERR_INVALID_ARG;
+        }
+        seg_len = seg;
+    }
+    const int S = seg_len;
     N_.resize(np);
     P_.resize(np);
     off64_.resize(np);
@@ -344,6 +463,7 @@ SwArgs<T> SweepEngine<T>::args(const Level &L, int which) const
     a.zxC = zxC_;
     a.zin = zin_;
     a.err = err_;
+    a.S = seg_len;
     return a;
 }
 

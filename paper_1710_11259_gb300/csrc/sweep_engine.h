@@ -19,9 +19,11 @@ class SweepEngine {
 public:
     // `ns`: problem sizes (caller packing: problem after problem, each problem's nrhs
     // n x n matrices back to back).  `tight`: shifts from the Sturm-bisection interval
-    // of A~ instead of Lemma B.2's.  Returns an fps_status; on error `err` holds a message.
+    // of A~ instead of Lemma B.2's.  `seg`: segment length of the partitioned sweeps
+    // (64 or 128 for FP32, 64 for FP64); seg <= 0 lets the autotuner pick it (FP32).
+    // Returns an fps_status; on error `err` holds a message.
     int create(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight, cudaStream_t setup_stream,
-               std::string &err);
+               std::string &err, int seg = 0);
     void release();
 
     // Solve for device pointers F, X (packed as above) on stream st.  FP32: returns
@@ -42,6 +44,8 @@ public:
     int64_t launches_last = 0;
     int max_rounds = 8;
     std::vector<std::vector<double>> shifts;  // level-0 shifts per problem
+    int seg_len = 0;                          // segment length in use
+    std::vector<float> tune_ms;               // autotuner timings per candidate (ms), if it ran
     int64_t total_elems() const { return tot64_; }
 
 private:
@@ -57,6 +61,8 @@ private:
         std::vector<cudaEvent_t> ev;  // 4 per iteration when instrumented
     };
     int build_graph(Level &L, std::string &err);
+    int autotune(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight, std::string &err);
+    int time_level(size_t li, int reps, float &ms, std::string &err);
     SwArgs<T> args(const Level &L, int which) const;
     int solve_refine(const double *F, double *X, cudaStream_t st, std::string &err);
     int solve_plain(const double *F, double *X, cudaStream_t st, std::string &err);

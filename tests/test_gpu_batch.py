@@ -99,20 +99,20 @@ def test_batched_workload_512_problems(api):
 
 
 def test_autotuner_picks_and_caches(api, tmp_path, monkeypatch):
-    """The pass size is picked by timing candidates on the plan's own buffers, then cached."""
+    """The segment length is picked by timing complete candidate engines on the plan's
+    sizes, then cached per GPU and size list; the tuned plan still matches the oracle."""
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("FPS_AUTOTUNE_CACHE", str(cache))
     monkeypatch.delenv("FPS_AUTOTUNE", raising=False)
     ns = [300, 257, 64, 33]
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
     plan = api.plan_create_batched(ns, nrhs=2, tol=1e-10, precision="fp32_refine")
-    chosen = api.plan_info(plan)["pass_ctas"]
+    chosen = api.plan_info(plan)["seg_len"]
     api.plan_destroy(plan)
-    assert chosen in {4 * sms, 8 * sms, 16 * sms, 32 * sms}
+    assert chosen in {64, 128}
     lines = cache.read_text().split("\n")
     assert len([ln for ln in lines if ln.strip()]) == 1
     plan = api.plan_create_batched(ns, nrhs=2, tol=1e-10, precision="fp32_refine")
-    assert api.plan_info(plan)["pass_ctas"] == chosen
+    assert api.plan_info(plan)["seg_len"] == chosen
     F = torch.from_numpy(np.concatenate([inputs.square_rhs(n, 60 + n).ravel() for n in ns for _ in range(2)])).cuda()
     X = api.poisson_square_solve(plan, F)
     torch.cuda.synchronize()
@@ -126,3 +126,28 @@ def test_autotuner_picks_and_caches(api, tmp_path, monkeypatch):
             Xo = oracle.poisson_square(f[o:o + n * n].reshape(n, n), 1e-13)
             assert _relmax(x[o:o + n * n].reshape(n, n), Xo) <= TOL_REFINE
             o += n * n
+
+
+@pytest.mark.parametrize("seg", ["64", "128"])
+def test_both_segment_lengths_match_oracle(api, tmp_path, monkeypatch, seg):
+    """Each compiled segment length, forced through the cache, on sizes with a short
+    last segment (n = 200, 321) and a single segment (n = 33)."""
+    ns = [321, 200, 33]
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("FPS_AUTOTUNE_CACHE", str(cache))
+    monkeypatch.delenv("FPS_AUTOTUNE", raising=False)
+    plan = api.plan_create_batched(ns, nrhs=1, tol=1e-10, precision="fp32_refine")
+    key = cache.read_text().split()[0]
+    api.plan_destroy(plan)
+    cache.write_text(f"{key} {seg}\n")
+    plan = api.plan_create_batched(ns, nrhs=1, tol=1e-10, precision="fp32_refine")
+    assert api.plan_info(plan)["seg_len"] == int(seg)
+    rng = np.random.default_rng(77)
+    rhs = [rng.standard_normal((1, n, n)) * inputs.decay_weights(n, 2)[None, :, None] *
+           inputs.decay_weights(n, 2)[None, None, :] for n in ns]
+    X = api.poisson_square_solve(plan, torch.from_numpy(_pack(rhs)).cuda())
+    torch.cuda.synchronize()
+    api.plan_destroy(plan)
+    Xs = _unpack(X.cpu().numpy(), ns, 1)
+    for p, n in enumerate(ns):
+        assert _relmax(Xs[p][0], oracle.poisson_square(rhs[p][0], 1e-13)) <= TOL_REFINE, n
