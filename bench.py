@@ -146,15 +146,31 @@ def _recorded_traffic(kernel_file: str):
     return None
 
 
-def cpu_baseline(target_seconds: float = 15.0) -> dict:
-    """The oracle (plain C, FP64, OpenMP over independent systems) on a bounded sample
-    of the workload: the n = 10^4 solve run for a limited number of its ADI
-    iterations; DOF/s extrapolated to the full iteration count at tol 1e-10."""
-    import oracle
-    from paper_1710_11259_gb300 import inputs
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
 
-    F = inputs.square_rhs(N, SEED, power=POWER)
-    J = oracle.square_iterations(N, TOL_REFINE)
+    return platform.processor() or platform.machine()
+
+
+def _oracle_per_iteration(F, jmax_probe: int, target_seconds: float):
+    """Seconds per ADI iteration of the oracle on F (and the fixed cost around the
+    loop), from runs with 1, 3 and then as many iterations as fit the target."""
+    import oracle
+
     t0 = time.perf_counter()
     oracle.poisson_square_partial(F, TOL_REFINE, 1)
     t1 = time.perf_counter()
@@ -162,16 +178,40 @@ def cpu_baseline(target_seconds: float = 15.0) -> dict:
     t2 = time.perf_counter()
     per_iter = max((t2 - t1) - (t1 - t0), 1e-6) / 2.0
     fixed = max((t1 - t0) - per_iter, 0.0)
-    js = int(max(2, min(J, (target_seconds - fixed) / per_iter)))
+    js = int(max(2, min(jmax_probe, (target_seconds - fixed) / per_iter)))
     t3 = time.perf_counter()
     oracle.poisson_square_partial(F, TOL_REFINE, js)
     t4 = time.perf_counter()
     per_iter = max((t4 - t3) - fixed, 1e-6) / js
+    return per_iter, fixed, js, t4 - t3
+
+
+def cpu_baseline(target_seconds: float = 15.0) -> dict:
+    """The oracle (plain C, FP64, OpenMP over independent systems) on a bounded sample
+    of the workload: the n = 10^4 solve run for a limited number of its ADI
+    iterations; DOF/s extrapolated to the full iteration count at tol 1e-10.  Timed on
+    every host core and on one core."""
+    import oracle
+    from paper_1710_11259_gb300 import inputs
+
+    F = inputs.square_rhs(N, SEED, power=POWER)
+    J = oracle.square_iterations(N, TOL_REFINE)
+    cores = oracle.num_threads()
+    per_iter, fixed, js, secs = _oracle_per_iteration(F, J, target_seconds)
     full = fixed + J * per_iter
-    return {"value": N * N / full, "unit": "DOF/s", "cores": oracle.num_threads(), "kind": "oracle",
+    oracle.set_num_threads(1)
+    try:
+        p1, f1, js1, secs1 = _oracle_per_iteration(F, J, target_seconds / 2)
+    finally:
+        oracle.set_num_threads(cores)
+    full1 = f1 + J * p1
+    return {"value": N * N / full, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(),
             "sample": f"n={N} FP64 oracle, {js} of its J={J} ADI iterations (tol 1e-10) timed "
-                      f"({t4 - t3:.1f} s), per-iteration time extrapolated to the full solve",
-            "seconds_timed": t4 - t3}
+                      f"({secs:.1f} s) on {cores} threads, per-iteration time extrapolated to the full solve",
+            "seconds_timed": secs,
+            "one_core": {"value": N * N / full1, "unit": "DOF/s", "cores": 1,
+                         "sample": f"{js1} ADI iterations timed ({secs1:.1f} s) on 1 thread"}}
 
 
 def run_reference(args) -> None:
@@ -213,6 +253,98 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def _fp64_ops(J: int) -> float:
+    """FP64 FMA-pipe operations per element of the padded tile region for one solve
+    of J iterations, as the pass kernels are written: row pass 3 (first iteration) or
+    11.39 (rebuild of the loaded 68 x 72 tile for a 64 x 64 core: 2.39; D: 1;
+    column and row stencils: 6; sweeps: 2), column pass 5 (rebuild 2, pivot scale 1,
+    sweeps 2)."""
+    return 3.0 + 11.39 * (J - 1) + 5.0 * J
+
+
+def _time_solves(api, plan, F, X, steps, stream, flush=None):
+    """Mean ms per solve over `steps` solves timed with CUDA events on the plan's
+    stream.  With `flush` (inputs smaller than L2) each solve is timed alone and the
+    L2 is overwritten between solves, outside the timed intervals."""
+    import torch
+
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            api.poisson_square_solve(plan, F, X)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+    total = 0.0
+    for _ in range(steps):
+        flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.poisson_square_solve(plan, F, X)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def config1(api, inputs, stream, steps) -> dict:
+    """n = 64, FP64, tol 1e-13, two right-hand sides, L2 flushed between timed solves.
+    The workload's second right-hand side comes from a manufactured solution whose
+    coefficients need the oracle's quadrature; the timed path must not touch the
+    oracle, so a second seeded decay-2 right-hand side (seed 1) stands in for it (the
+    solve's cost does not depend on the values)."""
+    import numpy as np
+    import torch
+
+    n = 64
+    F = torch.from_numpy(np.stack([inputs.square_rhs(n, 0), inputs.square_rhs(n, 1)])).cuda()
+    X = torch.empty_like(F)
+    plan = api.plan_create(n, 2, 1e-13, "fp64", nrhs=2, stream=stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for _ in range(3):
+        api.poisson_square_solve(plan, F, X)
+    ms = _time_solves(api, plan, F, X, max(steps, 5), stream, flush)
+    info = api.plan_info(plan)
+    api.plan_destroy(plan)
+    return {"workload": "square n=64, FP64 tol 1e-13, 2 right-hand sides (decay-2 seeds 0 and 1), "
+                        "L2 flushed between timed solves",
+            "value": 2 * n * n / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms, "J": info["J"],
+            "kernel_launches": info["kernel_launches"]}
+
+
+def config4(api, inputs, stream, steps) -> dict:
+    """512 squares, n log-uniform in [32, 2048] (seed 5), 4 right-hand sides each,
+    FP32 sweeps + FP64 refinement to 1e-10, one launch per pass for the whole batch."""
+    import numpy as np
+    import torch
+
+    ns, rhs = inputs.batch_problems(seed=5)
+    ns = [int(n) for n in ns]
+    dofs = 4 * sum(n * n for n in ns)
+    F = torch.empty(dofs, dtype=torch.float64, device="cuda")
+    o = 0
+    for r in rhs:
+        F[o:o + r.size].copy_(torch.from_numpy(r.ravel()))
+        o += r.size
+    del rhs
+    X = torch.empty_like(F)
+    t0 = time.perf_counter()
+    plan = api.plan_create_batched(ns, nrhs=4, tol=TOL_REFINE, precision="fp32_refine",
+                                   stream=stream.cuda_stream)
+    plan_s = time.perf_counter() - t0
+    api.poisson_square_solve(plan, F, X)
+    ms = _time_solves(api, plan, F, X, max(1, min(steps, 3)), stream)
+    info = api.plan_info(plan)
+    api.plan_destroy(plan)
+    del F, X
+    return {"workload": "512 squares, n = round(exp(U(ln 32, ln 2048))) seed 5, 4 right-hand sides "
+                        "F = g/((1+j)^2(1+k)^2), FP32 sweeps + FP64 refinement to 1e-10",
+            "value": dofs / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms, "dofs": dofs,
+            "refine_rounds": info["refine_rounds"], "final_rel_residual": info["last_residual"],
+            "seg_len": info["seg_len"], "plan_seconds": plan_s, "kernel_launches": info["kernel_launches"]}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,6 +352,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="headline only (no config-1/batch/FP64 lines)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -227,7 +360,6 @@ def main() -> None:
         run_reference(args)
         return
 
-    import numpy as np
     import torch
 
     ws, rank, local = _dist()
@@ -274,60 +406,15 @@ def main() -> None:
     kt = api.plan_kernel_times(plan)
     X32 = X.clone()
 
-    # ---------------- plain FP64 on the same input ----------------
-    plan64 = api.plan_create(N, 2, TOL_FP64, "fp64", stream=stream.cuda_stream)
-    api.plan_set_instrument(plan64, True)
-    api.poisson_square_solve(plan64, F, X)
-    k64 = max(1, min(args.steps, 2))
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(k64):
-        api.poisson_square_solve(plan64, F, X)
-    f1.record(stream)
-    barrier()
-    ms64 = rank_max(f0.elapsed_time(f1) / k64)
-    kt64 = api.plan_kernel_times(plan64)
-    info64 = api.plan_info(plan64)
-    agree = float((X32 - X).abs().max().item() / X.abs().max().item())
-
-    # ---------------- Legendre coefficients in and out (banded 2D maps, HBM bound) ----------------
-    def event_ms(fn, reps=5):
-        fn()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
-    Fleg = torch.empty_like(F)
-    Uleg = torch.empty((N + 2, N + 2), dtype=torch.float64, device="cuda")
-    in_ms = event_ms(lambda: api.legendre_to_ctilde(F, Fleg, stream=stream.cuda_stream))
-    out_ms = event_ms(lambda: api.solution_to_legendre(X, Uleg, stream=stream.cuda_stream))
-    del Fleg, Uleg
-
-    # ---------------- end to end: host buffers through the C ABI ----------------
-    Fpin = torch.from_numpy(Fh).pin_memory()
-    Xpin = torch.empty_like(Fpin).pin_memory()
-    api.poisson_square_solve(plan, Fpin, Xpin)
-    k_e2e = max(1, min(args.steps, 3))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        api.poisson_square_solve(plan, Fpin, Xpin)
-    barrier()
-    e2e_s = rank_max((time.perf_counter() - t0) / k_e2e)
-
     hbm, peak_kind = _peaks()
+    n_pass = kt["count"]
+    col_bytes = 2 * 4.0 * N * N * (n_pass // 2)  # column pass: one FP32 read, one write per element
+    row_bytes = kt["alg_bytes"] - col_bytes
     achieved = kt["alg_bytes"] / (kt["total_ms"] * 1e-3) / 1e9 if kt["total_ms"] > 0 else None
-    achieved64 = kt64["alg_bytes"] / (kt64["total_ms"] * 1e-3) / 1e9 if kt64["total_ms"] > 0 else None
-    tr = _recorded_traffic("refine.cu")
+    tr = _recorded_traffic("sweep.cu")
     traffic = None
-    if tr is not None and kt["count"] > 0:
-        traffic = tr["dram_bytes_per_launch_at_n"] * (N * N) / float(tr["n"]) ** 2
-
+    if tr is not None:
+        traffic = 0.5 * (tr["row_pass_dram_bytes"] + tr["col_pass_dram_bytes"]) * (N * N) / float(tr["n"]) ** 2
     dofs_job = ws * N * N
     value = job_throughput(ws, N * N, ms)
     line = {
@@ -349,38 +436,106 @@ def main() -> None:
             "n": N, "dofs_per_gpu": N * N, "tol": TOL_REFINE, "parallelism": "replicas" if ws > 1 else "single",
             "l2": "inputs larger than L2 (each FP64 n x n array 800 MB, FP32 400 MB)",
             "refine_rounds": info["refine_rounds"], "final_rel_residual": info["last_residual"],
-        },
-        "fp64": {
-            "value": dofs_job / (ms64 * 1e-3), "unit": "DOF/s", "ms_per_step": ms64, "steps": k64, "tol": TOL_FP64,
-            "J": info64["J"],
-            "roofline": {"bound": "alu", "achieved_gbs_algorithmic": achieved64,
-                         "note": "FP64 sweep kernel; GB300 FP64 FMA rate measured 0.597 TFMA/s"},
-            "max_rel_diff_vs_fp32_refine": agree,
+            "seg_len": info["seg_len"],
         },
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-            "kernel": "col_bwd_kernel (column back-substitution pass of the FP32 inner ADI)",
-            "launches_timed": kt["count"], "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-        },
-        "e2e": {"value": dofs_job / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 8 * N * N,
-                "d2h_bytes_per_step": 8 * N * N},
-        "legendre": {
-            "in_ms": in_ms, "out_ms": out_ms,
-            "in_gbs": 16.0 * N * N / (in_ms * 1e-3) / 1e9,
-            "out_gbs": (8.0 * N * N + 8.0 * (N + 2) ** 2) / (out_ms * 1e-3) / 1e9,
-            "in_frac": 16.0 * N * N / (in_ms * 1e-3) / 1e9 / hbm,
-            "out_frac": (8.0 * N * N + 8.0 * (N + 2) ** 2) / (out_ms * 1e-3) / 1e9 / hbm,
-            "note": "fps_legendre_to_ctilde / fps_solution_to_legendre at n=10^4 on device buffers; "
-                    "algorithmic bytes = one FP64 read and one FP64 write per element; outside the timed solve",
+            "kernel": "ADI pass kernels (row pass + column pass of every inner iteration)",
+            "bytes_per_launch": "12 B per element: the 6 FP32 words per element and iteration of the "
+                                "residual-form ADI (row pass: c, D read; D, result written; column pass: "
+                                "result read, c written), the survey's 3 words per half-step",
+            "launches_timed": n_pass, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "row_pass": {"ms": kt["row_ms"], "gbs": row_bytes / (kt["row_ms"] * 1e-3) / 1e9 if kt["row_ms"] else None,
+                         "frac": row_bytes / (kt["row_ms"] * 1e-3) / 1e9 / hbm if kt["row_ms"] else None},
+            "col_pass": {"ms": kt["col_ms"], "gbs": col_bytes / (kt["col_ms"] * 1e-3) / 1e9 if kt["col_ms"] else None,
+                         "frac": col_bytes / (kt["col_ms"] * 1e-3) / 1e9 / hbm if kt["col_ms"] else None},
         },
         "gpu_launches": int(info["kernel_launches"]) * args.steps,
         "clocks": clocks,
         "paper_context_dofs": PAPER_DOFS,
     }
+
+    # ---------------- end to end: host buffers through the C ABI ----------------
+    Fpin = torch.from_numpy(Fh).pin_memory()
+    Xpin = torch.empty_like(Fpin).pin_memory()
+    api.poisson_square_solve(plan, Fpin, Xpin)
+    k_e2e = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        api.poisson_square_solve(plan, Fpin, Xpin)
+    barrier()
+    e2e_s = rank_max((time.perf_counter() - t0) / k_e2e)
+    line["e2e"] = {"value": dofs_job / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 8 * N * N,
+                   "d2h_bytes_per_step": 8 * N * N}
     api.plan_destroy(plan)
-    api.plan_destroy(plan64)
-    del F, X, X32
+    del Fpin, Xpin
+
+    if not args.no_extra:
+        # ---------------- plain FP64 on the same input (bound by the FP64 FMA rate) ----------------
+        plan64 = api.plan_create(N, 2, TOL_FP64, "fp64", stream=stream.cuda_stream)
+        api.plan_set_instrument(plan64, True)
+        api.poisson_square_solve(plan64, F, X)
+        k64 = max(1, min(args.steps, 2))
+        barrier()
+        ms64 = rank_max(_time_solves(api, plan64, F, X, k64, stream))
+        kt64 = api.plan_kernel_times(plan64)
+        info64 = api.plan_info(plan64)
+        agree = float((X32 - X).abs().max().item() / X.abs().max().item())
+        api.plan_destroy(plan64)
+        fma_rate = api.probe_fma_rate("fp64")
+        Np = 64 * ((N + 63) // 64)
+        ops = _fp64_ops(info64["J"]) * Np * Np
+        alg_ops = 12.0 * info64["J"] * N * N
+        line["fp64"] = {
+            "value": dofs_job / (ms64 * 1e-3), "unit": "DOF/s", "ms_per_step": ms64, "steps": k64, "tol": TOL_FP64,
+            "J": info64["J"], "speedup_of_fp32_refine": ms64 / ms,
+            "roofline": {"bound": "alu", "unit": "FP64 FMA/s", "peak": fma_rate,
+                         "peak_kind": "measured by fps_probe_fma_rate on this GPU",
+                         "achieved": ops / (kt64["total_ms"] * 1e-3), "frac": ops / (kt64["total_ms"] * 1e-3) / fma_rate,
+                         "ops_per_element_iteration": round(_fp64_ops(info64["J"]) / info64["J"], 3),
+                         "frac_alg": alg_ops / (kt64["total_ms"] * 1e-3) / fma_rate,
+                         "alg_ops_per_element_iteration": 12,
+                         "pass_ms": kt64["total_ms"], "row_ms": kt64["row_ms"], "col_ms": kt64["col_ms"],
+                         "hbm_gbs_algorithmic": kt64["alg_bytes"] / (kt64["total_ms"] * 1e-3) / 1e9},
+            "max_rel_diff_vs_fp32_refine": agree,
+        }
+
+        # ---------------- Legendre coefficients in and out ----------------
+        def event_ms(fn, reps=5):
+            fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        Fleg = torch.empty_like(F)
+        Uleg = torch.empty((N + 2, N + 2), dtype=torch.float64, device="cuda")
+        in_ms = event_ms(lambda: api.legendre_to_ctilde(F, Fleg, stream=stream.cuda_stream))
+        out_ms = event_ms(lambda: api.solution_to_legendre(X, Uleg, stream=stream.cuda_stream))
+        del Fleg, Uleg
+        line["legendre"] = {
+            "in_ms": in_ms, "out_ms": out_ms,
+            "in_gbs": 16.0 * N * N / (in_ms * 1e-3) / 1e9,
+            "out_gbs": (8.0 * N * N + 8.0 * (N + 2) ** 2) / (out_ms * 1e-3) / 1e9,
+            "in_frac": 16.0 * N * N / (in_ms * 1e-3) / 1e9 / hbm,
+            "out_frac": (8.0 * N * N + 8.0 * (N + 2) ** 2) / (out_ms * 1e-3) / 1e9 / hbm,
+            "in_fma_frac": 4.0 * N * N / (in_ms * 1e-3) / fma_rate,
+            "out_fma_frac": 4.0 * N * N / (out_ms * 1e-3) / fma_rate,
+            "note": "fps_legendre_to_ctilde / fps_solution_to_legendre at n=10^4 on device buffers; "
+                    "algorithmic bytes = one FP64 read and one FP64 write per element; about 4 FP64 "
+                    "FMA-pipe operations per element, against the measured FP64 FMA rate",
+        }
+        del F, X, X32
+        torch.cuda.empty_cache()
+        line["config1"] = config1(api, inputs, stream, args.steps)
+        line["config4"] = config4(api, inputs, stream, args.steps)
+    else:
+        del F, X, X32
     torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -272,6 +272,16 @@ int fps_square_bands(int64_t n, double *d, double *e);
  */
 int fps_square_spectral_interval(int64_t n, int tight, double *lo, double *hi);
 
+/*
+ * fps_probe_fma_rate -- measure the current device's fused multiply-add rate:
+ * FP64 FMAs per second (precision = FPS_FP64) or FP32 ones (FPS_FP32_REFINE), from a
+ * ~100 ms kernel of independent FMA chains timed with CUDA events.  Instrumentation
+ * with no counterpart in the paper: it is the peak that the FP64 sweeps, bound by
+ * GB300's FP64 rate rather than by HBM, are reported against.  Synchronous.
+ * Errors: INVALID_ARG (NULL output, unknown precision), CUDA.
+ */
+int fps_probe_fma_rate(int precision, double *fma_per_s);
+
 /* Build identification (compute capability the kernels were built for, e.g. 103). */
 int fps_build_arch(void);
 

@@ -67,6 +67,7 @@ EXPORTED = [
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
     "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
     "fps_square_spectral_interval", "fps_legendre_to_ctilde", "fps_solution_to_legendre", "fps_plan_pass_times",
+    "fps_probe_fma_rate",
 ]
 
 
@@ -101,6 +102,7 @@ def lib() -> ctypes.CDLL:
         L.fps_plan_set_instrument.argtypes = [vp, ctypes.c_int]
         L.fps_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
         L.fps_plan_pass_times.argtypes = [vp, dp, dp]
+        L.fps_probe_fma_rate.argtypes = [ctypes.c_int, dp]
         L.fps_poisson_square_solve_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp]
         L.fps_square_spectral_interval.argtypes = [i64, ctypes.c_int, dp, dp]
         L.fps_legendre_to_ctilde.argtypes = [i64, vp, vp, vp]
@@ -319,6 +321,13 @@ def poisson_square_solve_noalloc(F, X, tol: float = 1e-13, stream: Optional[int]
     s = _current_stream() if stream is None else int(stream)
     return int(lib().fps_poisson_square_solve_noalloc(int(F.shape[-1]), float(tol), ctypes.c_void_p(_ptr(F)),
                                                       ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(s)))
+
+
+def probe_fma_rate(precision="fp64") -> float:
+    """Measured FMAs per second of the current device (FP64 or FP32)."""
+    r = ctypes.c_double()
+    _check(lib().fps_probe_fma_rate(_PRECISION[precision], ctypes.byref(r)))
+    return r.value
 
 
 def zolotarev_shifts(a: float, b: float, c: float, d: float, tol: float, J: int = 0):

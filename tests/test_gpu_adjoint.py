@@ -72,14 +72,22 @@ def test_gradcheck_small(mods):
     assert ok
 
 
-@pytest.mark.parametrize("n,precision", [(300, "fp64"), (300, "fp32_refine"), (10000, "fp32_refine")])
-def test_adjoint_against_central_differences(mods, n, precision):
-    """Config of the n = 10^4 workload: F = g/((1+j)(1+k)) seed 3, U* seed 4, 16 FD directions (seed 7)."""
+@pytest.mark.parametrize("n,precision,tol", [(300, "fp64", 1e-13), (300, "fp32_refine", 1e-10),
+                                             (10000, "fp64", 1e-13), (10000, "fp32_refine", 1e-12)])
+def test_adjoint_against_central_differences(mods, n, precision, tol):
+    """Config of the n = 10^4 workload: F = g/((1+j)(1+k)) seed 3, U* seed 4, 16 FD directions (seed 7).
+
+    L is exactly quadratic in F, so the central difference carries no truncation
+    error; what it does carry is the forward solve's departure from linearity,
+    about tol relative to |X| at F0 +- hV, divided by the cosine between X - U*
+    and the solve of V.  At n = 10^4 that cosine is small enough that the refined
+    solve's 1e-10 stop leaves the quotient at ~1e-6 of the directional derivative,
+    so the refined case is checked with the refinement run to 1e-12."""
     api, autograd = mods
     F0 = torch.from_numpy(inputs.square_rhs(n, 3, power=1)).cuda()
     Ustar = torch.from_numpy(inputs.gaussian(4, (n, n))).cuda()
     V = inputs.unit_directions(7, 16, (n, n))
-    plan = api.plan_create(n, 2, 1e-13 if precision == "fp64" else 1e-10, precision)
+    plan = api.plan_create(n, 2, tol, precision)
 
     def loss(F):
         X = autograd.poisson_square(F, plan)
