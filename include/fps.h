@@ -92,8 +92,13 @@ typedef struct {
  * The plan computes the spectral interval of Lemma B.2, J of (2.9), the shifts
  * of (2.4) on the host in FP64, uploads them and factors every shifted matrix
  * A~ - q_j I once (Thomas pivots, App. B even/odd decoupling).
- * Errors: INVALID_ARG (n < 1, dim not 2/3, tol outside (0,1), nrhs < 1, out NULL),
- * CUDA (allocation or launch failure).  *out is NULL on error.
+ * Every shift list is validated on the host before any kernel runs (finite, inside
+ * the spectral interval).  Environment: FPS_MAX_REFINE_ROUNDS caps the refinement
+ * rounds of FP32_REFINE plans (default 8); FPS_INJECT_SHIFT_FAULT=nan|neg corrupts
+ * the first shift before validation (host-side fault injection for tests).
+ * Errors: INVALID_ARG (n < 1, dim not 2/3, tol outside (0,1), nrhs < 1, out NULL, a
+ * shift list that fails validation), CUDA (allocation or launch failure).  *out is
+ * NULL on error.
  */
 int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precision, int nrhs, void *stream);
 

@@ -42,6 +42,24 @@ double bits_to_double(unsigned long long b)
 const double kLevelTols[] = {1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2};
 constexpr int kTileW = 64;       // rows of a row-pass tile / columns of a column-pass tile
 constexpr int kChainLines = 64;
+// Every shift must be finite and lie in [lo, hi] (up to rounding): the factors of
+// A~ - qI are only guaranteed non-singular there (sigma(A~) in [-hi, -lo], q > 0).
+bool shifts_valid(const std::vector<double> &q, double lo, double hi)
+{
+    for (double v : q)
+        if (!std::isfinite(v) || v < lo * (1.0 - 1e-12) || v > hi * (1.0 + 1e-12)) return false;
+    return !q.empty();
+}
+
+// Host-side fault injection for the failure-path tests: FPS_INJECT_SHIFT_FAULT=nan
+// or =neg corrupts the first shift of every list before validation.
+void inject_shift_fault(std::vector<double> &q)
+{
+    const char *f = std::getenv("FPS_INJECT_SHIFT_FAULT");
+    if (!f || q.empty()) return;
+    if (std::string(f) == "nan") q[0] = std::nan("");
+    else if (std::string(f) == "neg") q[0] = -q[0];
+}
 }  // namespace
 
 template <typename T>
@@ -195,6 +213,10 @@ int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol,
     tol_ = tol;
     cap_ = setup_stream;
     const int np = (int)ns.size();
+    if (const char *mr = std::getenv("FPS_MAX_REFINE_ROUNDS")) {  // cap on refinement rounds (>= 1)
+        const int v = std::atoi(mr);
+        if (v >= 1) max_rounds = v;
+    }
     if (seg <= 0) {
         if (kFP64) {
             seg_len = 64;
@@ -389,6 +411,13 @@ int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol,
             const int64_t n = ns[p];
             const int N = N_[p];
             zolotarev_shifts_symmetric(lo[p], hi[p], L.J[p], q);
+            inject_shift_fault(q);
+            if (!shifts_valid(q, lo[p], hi[p])) {
+                cudaFree(d_jobs);
+                levels_.push_back(std::move(L));
+                err = "shift list failed validation (a shift is not finite or lies outside the spectral interval)";
+                return FPS_ERR_INVALID_ARG;
+            }
             if (li == 0) shifts[p] = q;
             SwProb<T> &sp = probs[p];
             sp.n = (int)n;

@@ -73,16 +73,16 @@ def test_gradcheck_small(mods):
 
 
 @pytest.mark.parametrize("n,precision,tol", [(300, "fp64", 1e-13), (300, "fp32_refine", 1e-10),
-                                             (10000, "fp64", 1e-13), (10000, "fp32_refine", 1e-12)])
+                                             (10000, "fp64", 1e-13)])
 def test_adjoint_against_central_differences(mods, n, precision, tol):
     """Config of the n = 10^4 workload: F = g/((1+j)(1+k)) seed 3, U* seed 4, 16 FD directions (seed 7).
 
     L is exactly quadratic in F, so the central difference carries no truncation
-    error; what it does carry is the forward solve's departure from linearity,
-    about tol relative to |X| at F0 +- hV, divided by the cosine between X - U*
-    and the solve of V.  At n = 10^4 that cosine is small enough that the refined
-    solve's 1e-10 stop leaves the quotient at ~1e-6 of the directional derivative,
-    so the refined case is checked with the refinement run to 1e-12."""
+    error; with h ||V|| = 10 ||F|| its FP64 rounding stays near 1e-7 at n = 10^4.  The
+    FP32-refined solve is linear only to its accuracy, which this quotient amplifies
+    to ~1e-6 at n = 10^4 whatever the stopping tolerance (measured 1.6e-6 at 1e-10
+    and 1.05e-6 at 1e-12), so its n = 10^4 gradient is checked against the FP64
+    gradient instead (next test)."""
     api, autograd = mods
     F0 = torch.from_numpy(inputs.square_rhs(n, 3, power=1)).cuda()
     Ustar = torch.from_numpy(inputs.gaussian(4, (n, n))).cuda()
@@ -109,3 +109,23 @@ def test_adjoint_against_central_differences(mods, n, precision, tol):
             worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * gnorm))
     api.plan_destroy(plan)
     assert worst <= 1e-6, worst
+
+
+def test_refined_gradient_matches_fp64_gradient_n10000(mods):
+    """dL/dF through the FP32-refined solve (tol 1e-10) against dL/dF through the FP64
+    solve at n = 10^4, element by element: both are the adjoint solve of X - U*."""
+    api, autograd = mods
+    n = 10000
+    F0 = torch.from_numpy(inputs.square_rhs(n, 3, power=1)).cuda()
+    Ustar = torch.from_numpy(inputs.gaussian(4, (n, n))).cuda()
+    grads = {}
+    for precision, tol in (("fp64", 1e-13), ("fp32_refine", 1e-10)):
+        plan = api.plan_create(n, 2, tol, precision)
+        F = F0.clone().requires_grad_(True)
+        X = autograd.poisson_square(F, plan)
+        (0.5 * ((X - Ustar) ** 2).sum()).backward()
+        grads[precision] = F.grad.detach()
+        api.plan_destroy(plan)
+        del X, F
+    err = float((grads["fp32_refine"] - grads["fp64"]).abs().max() / grads["fp64"].abs().max())
+    assert err <= 1e-10, err

@@ -90,12 +90,15 @@ def test_batched_workload_512_problems(api):
     api.plan_destroy(plan)
     assert info["batch"] == 512 and info["last_residual"] <= 1e-10
     Xs = _unpack(X.cpu().numpy(), ns, 4)
-    order = np.argsort(ns)
-    sample = [order[0], order[1], order[len(ns) // 2], order[-2], order[-1]]
-    for p in sample:
-        r = int(p) % 4
-        Xo = oracle.poisson_square(rhs[p][r], 1e-13)
-        assert _relmax(Xs[p][r], Xo) <= TOL_REFINE, (ns[p], r)
+    del X, F
+    # every one of the 2048 (problem, right-hand side) pairs, element by element
+    worst = 0.0
+    for p in range(len(ns)):
+        for r in range(4):
+            e = _relmax(Xs[p][r], oracle.poisson_square(rhs[p][r], 1e-13))
+            worst = max(worst, e)
+            assert e <= TOL_REFINE, (p, ns[p], r, e)
+    assert worst <= TOL_REFINE
 
 
 def test_autotuner_picks_and_caches(api, tmp_path, monkeypatch):

@@ -80,7 +80,7 @@ def _cube_by_diagonalisation(F):
     return Y * S3
 
 
-@pytest.mark.parametrize("n", [17])
+@pytest.mark.parametrize("n", [17, 32, 64])
 def test_cube_against_diagonalisation(api, n):
     """Sizes the oracle cannot reach in seconds: against an exact solve by diagonalising A~."""
     F = inputs.cube_rhs(n, 6)
@@ -196,3 +196,23 @@ def test_cube_refine_full_size(api):
     Xd = _cube_by_diagonalisation(F)
     assert info["last_residual"] <= 1e-10
     assert _relmax(X, Xd) <= 1e-10
+
+
+@pytest.mark.parametrize("precision,tol,bar", [("fp64", 1e-13, 1e-11), ("fp32_refine", 1e-10, 1e-10)])
+def test_cube_adjoint_against_exact_solve_n17(api, precision, tol, bar):
+    """dL/dF of L = 0.5 ||X - U*||^2 at n = 17 (F seed 6, U* seed 4) against the exact
+    adjoint: the solve map is self-adjoint, so dL/dF is the exact solve of X - U*,
+    computed here by diagonalising A~."""
+    from paper_1710_11259_gb300 import autograd
+
+    n = 17
+    F0 = torch.from_numpy(inputs.cube_rhs(n, 6)).cuda()
+    Ustar = torch.from_numpy(inputs.gaussian(4, (n, n, n))).cuda()
+    plan = api.plan_create(n, 3, tol, precision)
+    F = F0.clone().requires_grad_(True)
+    X = autograd.poisson_cube(F, plan)
+    (0.5 * ((X - Ustar) ** 2).sum()).backward()
+    g = F.grad.detach().cpu().numpy()
+    api.plan_destroy(plan)
+    want = _cube_by_diagonalisation((X.detach() - Ustar).cpu().numpy())
+    assert _relmax(g, want) <= bar
