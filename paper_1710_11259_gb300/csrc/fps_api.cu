@@ -1,6 +1,7 @@
 // C ABI of the solver (include/fps.h): plans, solves, adjoint, host helpers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,7 @@
 #include "../../include/fps.h"
 #include "host_math.h"
 #include "sweep_engine.h"
+#include "small.cuh"
 #include "cube.h"
 #include "legendre.cuh"
 #include "trace.h"
@@ -80,6 +82,9 @@ struct fps_plan {
     // square: the ADI pass engine (FP32 sweeps + FP64 refinement, or plain FP64)
     fps::SweepEngine<float> *eng32 = nullptr;
     fps::SweepEngine<double> *eng64 = nullptr;
+    // FP64 squares with n <= 64: whole ADI in one launch (cluster kernel, warp-shuffle PCR)
+    bool small = false;
+    double *sm_bands = nullptr, *sm_q = nullptr, *sm_pcr = nullptr;
     // dim = 3: the nested cube ADI
     fps::CubeEngine *cube = nullptr;
     std::vector<int64_t> batch_ns;   // sizes of a batched plan (empty otherwise)
@@ -98,6 +103,9 @@ void release(fps_plan *p)
     DeviceGuard g(p->device);
     if (p->stage_in) cudaFree(p->stage_in);
     if (p->stage_out) cudaFree(p->stage_out);
+    if (p->sm_bands) cudaFree(p->sm_bands);
+    if (p->sm_q) cudaFree(p->sm_q);
+    if (p->sm_pcr) cudaFree(p->sm_pcr);
     if (p->eng32) {
         p->eng32->release();
         delete p->eng32;
@@ -145,6 +153,44 @@ int solve_engine(fps_plan *p, E *eng, const double *F, double *X, bool fdev, boo
     return FPS_OK;
 }
 
+// FP64, n <= 64: one launch of the cluster kernel for all right-hand sides.
+int solve_small(fps_plan *p, const double *F, double *X, bool fdev, bool xdev, const char *what)
+{
+    const size_t bytes = sizeof(double) * (size_t)p->total_elems;
+    const double *Fd = F;
+    double *Xd = X;
+    if (!fdev) {
+        if (!p->stage_in) FPS_CK(cudaMalloc((void **)&p->stage_in, bytes));
+        FPS_CK(cudaMemcpyAsync(p->stage_in, F, bytes, cudaMemcpyHostToDevice, p->stream));
+        Fd = p->stage_in;
+    }
+    if (!xdev) {
+        if (!p->stage_out) FPS_CK(cudaMalloc((void **)&p->stage_out, bytes));
+        Xd = p->stage_out;
+    }
+    fps::SmallArgs a;
+    a.n = (int)p->n;
+    a.J = p->J;
+    a.nrhs = p->nrhs;
+    a.F = Fd;
+    a.X = Xd;
+    a.d = p->sm_bands;
+    a.e = p->sm_bands + p->n;
+    a.s = p->sm_bands + 2 * p->n;
+    a.q = p->sm_q;
+    a.pcr = p->sm_pcr;
+    cudaError_t e = fps::launch_small_adi(a, p->stream);
+    if (e != cudaSuccess) return fail(FPS_ERR_CUDA, std::string(what) + ": small-n kernel: " + cudaGetErrorString(e));
+    p->launches_last = 1;
+    if (!xdev) {
+        FPS_CK(cudaMemcpyAsync(X, Xd, bytes, cudaMemcpyDeviceToHost, p->stream));
+        FPS_CK(cudaStreamSynchronize(p->stream));
+    } else if (!fdev) {
+        FPS_CK(cudaStreamSynchronize(p->stream));
+    }
+    return FPS_OK;
+}
+
 int solve_square(fps_plan *p, const double *F, double *X, const char *what)
 {
     fps::TraceRange tr(what);
@@ -157,6 +203,7 @@ int solve_square(fps_plan *p, const double *F, double *X, const char *what)
     DeviceGuard g(p->device);
     const bool fdev = is_device_pointer(F), xdev = is_device_pointer(X);
     p->launches_last = 0;
+    if (p->small) return solve_small(p, F, X, fdev, xdev, what);
     if (p->eng32) return solve_engine(p, p->eng32, F, X, fdev, xdev, what);
     return solve_engine(p, p->eng64, F, X, fdev, xdev, what);
 }
@@ -235,7 +282,27 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     PCK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     std::string err;
     int st;
-    if (precision == FPS_FP64) {
+    if (precision == FPS_FP64 && n <= fps::kSmallMaxN) {
+        // whole ADI in one launch: bands, shifts and reduction coefficients on the device
+        std::vector<double> d, e, s, pcr;
+        fps::square_bands(n, d, e);
+        fps::inv_sqrt_E(n, s);
+        fps::small_pcr_coefficients(n, d, e, p->q, pcr);
+        std::vector<double> bands(3 * n);
+        std::copy(d.begin(), d.end(), bands.begin());
+        std::copy(e.begin(), e.end(), bands.begin() + n);
+        std::copy(s.begin(), s.end(), bands.begin() + 2 * n);
+        PCK(fps::small_setup_kernel());
+        PCK(cudaMalloc((void **)&p->sm_bands, sizeof(double) * 3 * n));
+        PCK(cudaMalloc((void **)&p->sm_q, sizeof(double) * p->J));
+        PCK(cudaMalloc((void **)&p->sm_pcr, sizeof(double) * pcr.size()));
+        PCK(cudaMemcpy(p->sm_bands, bands.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+        PCK(cudaMemcpy(p->sm_q, p->q.data(), sizeof(double) * p->J, cudaMemcpyHostToDevice));
+        PCK(cudaMemcpy(p->sm_pcr, pcr.data(), sizeof(double) * pcr.size(), cudaMemcpyHostToDevice));
+        p->bytes += (int64_t)sizeof(double) * (3 * n + p->J + (int64_t)pcr.size());
+        p->small = true;
+        st = FPS_OK;
+    } else if (precision == FPS_FP64) {
         p->eng64 = new fps::SweepEngine<double>();
         st = p->eng64->create(std::vector<int64_t>{n}, nrhs, tol, false, p->cap_stream, err);
         if (st == FPS_OK) p->bytes += p->eng64->bytes;
@@ -386,7 +453,8 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
 int fps_plan_set_instrument(fps_plan *p, int on)
 {
     if (!p) return fail(FPS_ERR_INVALID_ARG, "fps_plan_set_instrument: plan is NULL");
-    if (!p->eng32 && !p->eng64) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_set_instrument: square plans only");
+    if (!p->eng32 && !p->eng64)
+        return fail(FPS_ERR_UNSUPPORTED, "fps_plan_set_instrument: square plans on the pass kernels only");
     DeviceGuard g(p->device);
     FPS_CK(cudaStreamSynchronize(p->cap_stream));
     if (p->stream) FPS_CK(cudaStreamSynchronize(p->stream));

@@ -180,3 +180,35 @@ def test_square_refine_full_size_10000(api):
     F, Xo = _oracle_full(10000, 3, 1)
     X, info = _solve(api, F, tol=1e-10, precision="fp32_refine")
     assert _relmax(X, Xo) <= TOL_REFINE
+
+
+def test_small_n_path_every_size(api):
+    """FP64 squares with n <= 64 run the whole ADI in one launch (warp-shuffle cyclic
+    reduction, iterates in shared memory, one cluster per right-hand side): every n
+    from 1 to 64 (odd and even parity lengths, part-filled warps), two right-hand
+    sides each, against the oracle element by element."""
+    for n in range(1, 65):
+        F = np.stack([inputs.square_rhs(n, 100 + n), inputs.square_rhs(n, 300 + n, power=1)])
+        X, info = _solve(api, F, tol=1e-13, precision="fp64")
+        assert info["kernel_launches"] == 1, n
+        for r in range(2):
+            Xo = oracle.poisson_square(F[r], 1e-13)
+            assert _relmax(X[r], Xo) <= TOL_FP64, (n, r)
+
+
+def test_config1_small_path_dense_and_manufactured(api):
+    """The n = 64 workload's two right-hand sides in one plan: decay-2 seed 0 against a
+    dense Kronecker solve of (3.6), and the manufactured degree-10 solution."""
+    n = 64
+    F1 = inputs.square_rhs(n, 0)
+    F2, Xexact = basis.manufactured_square(basis.monomial_coeffs(inputs.poly_values(1), 10), n)
+    X, info = _solve(api, np.stack([F1, F2]), tol=1e-13, precision="fp64")
+    assert info["kernel_launches"] == 1
+    d, e = oracle.M_bands(n)
+    M = np.diag(d)
+    for j in range(n - 2):
+        M[j, j + 2] = M[j + 2, j] = e[j]
+    Dm = np.diag([-(j + 1.0) * (j + 2.0) for j in range(n)])
+    Xd = np.linalg.solve(np.kron(M, Dm) + np.kron(Dm, M), F1.ravel()).reshape(n, n)  # (3.6), dense
+    assert _relmax(X[0], Xd) <= TOL_FP64
+    assert _relmax(X[1], Xexact) <= 1e-12
