@@ -47,6 +47,13 @@ typedef enum {
     FPS_FP32_REFINE = 1  /* FP32 sweeps inside an FP64 iterative refinement of (3.9) */
 } fps_precision;
 
+/* Flag OR-ed into the precision argument of fps_plan_create: take the ADI shifts of
+ * an FPS_FP64 square from a tight spectral interval of A~ (Sturm-count bisection,
+ * fps_square_spectral_interval with tight != 0) instead of Lemma B.2's Gershgorin
+ * interval; the cross-ratio of (2.9) shrinks, and so does J (133 -> 110 at n = 10^4,
+ * tol 1e-13).  FPS_FP32_REFINE inner solves always use the tight interval. */
+#define FPS_TIGHT_SPECTRUM 0x100
+
 typedef enum {
     FPS_OK = 0,
     FPS_ERR_INVALID_ARG = -1,   /* bad size, tolerance, dimension, pointer */
@@ -86,7 +93,7 @@ typedef struct {
  *   tol        relative accuracy eps of Theorem 2.1, 0 < tol < 1 (App. A requires it).
  *              FP64: the ADI error bound ||Y - Y_J||_2 <= tol ||Y||_2 of (2.9).
  *              FP32_REFINE: target of max |R~| / max |F~| for the refinement.
- *   precision  fps_precision.
+ *   precision  fps_precision, optionally | FPS_TIGHT_SPECTRUM (squares).
  *   stream     cudaStream_t (may be NULL for the legacy default stream); the
  *              plan's device is the current device at the time of the call.
  * The plan computes the spectral interval of Lemma B.2, J of (2.9), the shifts

@@ -72,6 +72,9 @@ def _lib(variant: str = "double") -> ctypes.CDLL:
                                               ctypes.c_int, c_dp, c_dp, c_dp]
             lib.orc_poisson_square.argtypes = [ctypes.c_long, ctypes.c_double, c_dp, c_dp]
             lib.orc_poisson_square.restype = ctypes.c_int
+            lib.orc_poisson_square_tight.argtypes = [ctypes.c_long, ctypes.c_double, c_dp, c_dp]
+            lib.orc_poisson_square_tight.restype = ctypes.c_int
+            lib.orc_tight_interval.argtypes = [ctypes.c_long, c_dp, c_dp]
             lib.orc_poisson_square_partial.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_int, c_dp, c_dp]
             lib.orc_poisson_square_partial.restype = ctypes.c_int
             lib.orc_poisson_cube.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double, c_dp,
@@ -153,14 +156,26 @@ def adi_sylvester(s: int, Ad, Ae, Bd, Be, F, p, q, variant: str = "double") -> n
     return X
 
 
-def poisson_square(F, tol: float = 1e-13, variant: str = "double") -> np.ndarray:
-    """Solve M X D^T + D X M^T = F (eq. (3.6)) by Table 3.1 steps 2-3."""
+def poisson_square(F, tol: float = 1e-13, variant: str = "double", tight: bool = False) -> np.ndarray:
+    """Solve M X D^T + D X M^T = F (eq. (3.6)) by Table 3.1 steps 2-3 (shifts from
+    Lemma B.2's interval, or from ``tight_interval`` when ``tight``)."""
     F = _f64(F)
     n = F.shape[0]
     assert F.ndim == 2 and F.shape == (n, n)
     X = np.zeros_like(F)
-    _lib(variant).orc_poisson_square(n, tol, _ptr(F), _ptr(X))
+    if tight:
+        _lib(variant).orc_poisson_square_tight(n, tol, _ptr(F), _ptr(X))
+    else:
+        _lib(variant).orc_poisson_square(n, tol, _ptr(F), _ptr(X))
     return X
+
+
+def tight_interval(n: int):
+    """(lo, hi) with sigma(A~) in [-hi, -lo]: Sturm-count bisection on the even and odd
+    tridiagonals of A~, padded (lo = |lambda_max|/2, hi = min(1, 1.01 |lambda_min|))."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _lib().orc_tight_interval(int(n), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
 
 
 def poisson_square_partial(F, tol: float, jmax: int) -> np.ndarray:

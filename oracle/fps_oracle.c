@@ -393,6 +393,59 @@ void orc_adi_sylvester(long n, int s, const double *Ad, const double *Ae, const 
 }
 
 /* ------------------------------------------------------------------------- */
+/* A tighter spectral interval than Lemma B.2 (used only when asked for).      */
+/* The eigenvalues of A~ are those of its two decoupled tridiagonals (even and  */
+/* odd indices, App. B).  By Sylvester's law of inertia the number of           */
+/* eigenvalues below x equals the number of negative pivots of the LDL^T        */
+/* factorisation of T - x I, whose pivots follow the Sturm recurrence            */
+/*     u_0 = t_00 - x,   u_k = (t_kk - x) - t_{k,k-1}^2 / u_{k-1}.               */
+/* Bisection on that count brackets the extreme eigenvalues; the returned        */
+/* interval is padded (half the smallest magnitude, 1.01 times the largest,      */
+/* capped at Lemma B.2's 1) so that it contains the spectrum with margin.        */
+/* ------------------------------------------------------------------------- */
+static long negative_pivots(long n, const double *ad, const double *ae, double x)
+{
+    long neg = 0;
+    for (int par = 0; par < 2; ++par) {
+        double u = 0.0;
+        for (long i = par; i < n; i += 2) {
+            double next = ad[i] - x;
+            if (i >= 2) next -= ae[i - 2] * ae[i - 2] / (u != 0.0 ? u : 1e-300);
+            if (next == 0.0) next = -1e-300;
+            neg += next < 0.0;
+            u = next;
+        }
+    }
+    return neg;
+}
+
+void orc_tight_interval(long n, double *lo, double *hi)
+{
+    double *ad = malloc(sizeof(double) * (size_t)n), *ae = malloc(sizeof(double) * (size_t)(n > 2 ? n : 1));
+    orc_square_bands(n, ad, ae);
+    /* most negative eigenvalue: count(x) == 0 means no eigenvalue below x */
+    double left = -1.0, right = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        double mid = 0.5 * (left + right);
+        if (negative_pivots(n, ad, ae, mid) == 0) left = mid;
+        else right = mid;
+    }
+    /* eigenvalue closest to zero, on a logarithmic scale between eps/8 and 1:
+     * count(-exp(t)) == n means every eigenvalue lies below -exp(t) */
+    double nd = (double)n;
+    double tl = log(1.0 / (240.0 * nd * nd * nd * nd)), tr = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        double tm = 0.5 * (tl + tr);
+        if (negative_pivots(n, ad, ae, -exp(tm)) == n) tl = tm;
+        else tr = tm;
+    }
+    *lo = 0.5 * exp(tl);
+    *hi = 1.01 * (-left) < 1.0 ? 1.01 * (-left) : 1.0;
+    free(ad);
+    free(ae);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Section 3 end to end (Table 3.1, steps 2-3) for  M X D^T + D X M^T = F.     */
 /*   1. A~ = D_s^{-1} D^{-1} M D_s, B~ = -A~                     (3.8)-(3.9)   */
 /*   2. F~ = D_s^{-1} (D^{-1} F D^{-1}) D_s^{-1}                 (3.9)         */
@@ -402,7 +455,7 @@ void orc_adi_sylvester(long n, int s, const double *Ad, const double *Ae, const 
 /*   6. X = D_s Y D_s                                            (reading R2)  */
 /* F, X: n x n row-major, X_ij pairs C~_i(y) with C~_j(x).  Returns J.         */
 /* ------------------------------------------------------------------------- */
-static int poisson_square(long n, double tol, const real *F, real *X, double *shifts_q_out, int jmax)
+static int poisson_square(long n, double tol, const real *F, real *X, double *shifts_q_out, int jmax, int tight)
 {
     size_t nn = (size_t)n * (size_t)n;
     long ne = n > 2 ? n - 2 : 1;
@@ -422,6 +475,14 @@ static int poisson_square(long n, double tol, const real *F, real *X, double *sh
     double nd = (double)n;
     double eps_n = 1.0 / (30.0 * nd * nd * nd * nd);
     double a = -1.0, b = -eps_n, c = eps_n, d = 1.0;
+    if (tight) {
+        double tlo, thi;
+        orc_tight_interval(n, &tlo, &thi);
+        a = -thi;
+        b = -tlo;
+        c = tlo;
+        d = thi;
+    }
     int J = orc_adi_iterations(a, b, c, d, tol);
     double *p = malloc(sizeof(double) * (size_t)J), *q = malloc(sizeof(double) * (size_t)J);
     orc_adi_shifts(a, b, c, d, tol, J, p, q);
@@ -445,7 +506,20 @@ int orc_poisson_square(long n, double tol, const double *F, double *X)
     size_t nn = (size_t)n * (size_t)n;
     real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
     for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
-    int J = poisson_square(n, tol, Fr, Xr, NULL, 0);
+    int J = poisson_square(n, tol, Fr, Xr, NULL, 0, 0);
+    for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
+    free(Fr);
+    free(Xr);
+    return J;
+}
+
+/* The same solve with the shifts of the tight interval (orc_tight_interval). */
+int orc_poisson_square_tight(long n, double tol, const double *F, double *X)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
+    for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
+    int J = poisson_square(n, tol, Fr, Xr, NULL, 0, 1);
     for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
     free(Fr);
     free(Xr);
@@ -460,7 +534,7 @@ int orc_poisson_square_partial(long n, double tol, int jmax, const double *F, do
     size_t nn = (size_t)n * (size_t)n;
     real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
     for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
-    int J = poisson_square(n, tol, Fr, Xr, NULL, jmax);
+    int J = poisson_square(n, tol, Fr, Xr, NULL, jmax, 0);
     for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
     free(Fr);
     free(Xr);

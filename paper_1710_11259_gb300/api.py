@@ -20,7 +20,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfps.so")
 
 FPS_FP64 = 0
 FPS_FP32_REFINE = 1
-_PRECISION = {"fp64": FPS_FP64, "fp32_refine": FPS_FP32_REFINE, FPS_FP64: FPS_FP64, FPS_FP32_REFINE: FPS_FP32_REFINE}
+FPS_TIGHT_SPECTRUM = 0x100
+_PRECISION = {"fp64": FPS_FP64, "fp32_refine": FPS_FP32_REFINE, "fp64_tight": FPS_FP64 | FPS_TIGHT_SPECTRUM,
+              FPS_FP64: FPS_FP64, FPS_FP32_REFINE: FPS_FP32_REFINE}
 
 STATUS = {
     0: "FPS_OK",

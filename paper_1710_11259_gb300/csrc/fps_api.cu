@@ -221,8 +221,11 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
     if (dim != 2 && dim != 3) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: dim must be 2 or 3");
     if (!(tol > 0.0 && tol < 1.0)) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: tol must lie in (0, 1)");
     if (nrhs < 1) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: nrhs must be >= 1");
+    const bool tight = (precision & FPS_TIGHT_SPECTRUM) != 0;
+    precision &= ~FPS_TIGHT_SPECTRUM;
     if (precision != FPS_FP64 && precision != FPS_FP32_REFINE)
         return fail(FPS_ERR_INVALID_ARG, "fps_plan_create: unknown precision");
+    if (tight && dim != 2) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: FPS_TIGHT_SPECTRUM is for squares");
     if (dim == 3) {
         if (n > 320) return fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the cube supports n <= 320");
         fps_plan *p = new fps_plan();
@@ -273,10 +276,12 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
             return bail(fail(FPS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)));          \
     } while (0)
 
-    // Lemma B.2 interval, (2.9) J, (2.4) shifts (symmetric intervals: p_j = -q_j).
-    const double eps = fps::square_eps(n);
-    p->J = fps::adi_iterations(-1.0, -eps, eps, 1.0, tol);
-    fps::zolotarev_shifts_symmetric(eps, 1.0, p->J, p->q);
+    // Lemma B.2 interval (or the tight one), (2.9) J, (2.4) shifts (symmetric
+    // intervals: p_j = -q_j).
+    double lo = fps::square_eps(n), hi = 1.0;
+    if (tight && precision == FPS_FP64) fps::square_tight_interval(n, lo, hi);
+    p->J = fps::adi_iterations(-hi, -lo, lo, hi, tol);
+    fps::zolotarev_shifts_symmetric(lo, hi, p->J, p->q);
     if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the square supports n <= 40000"));
     if (nrhs > 256) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the square supports nrhs <= 256"));
     PCK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
@@ -304,7 +309,7 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
         st = FPS_OK;
     } else if (precision == FPS_FP64) {
         p->eng64 = new fps::SweepEngine<double>();
-        st = p->eng64->create(std::vector<int64_t>{n}, nrhs, tol, false, p->cap_stream, err);
+        st = p->eng64->create(std::vector<int64_t>{n}, nrhs, tol, tight, p->cap_stream, err);
         if (st == FPS_OK) p->bytes += p->eng64->bytes;
     } else {
         p->eng32 = new fps::SweepEngine<float>();

@@ -212,3 +212,31 @@ def test_config1_small_path_dense_and_manufactured(api):
     Xd = np.linalg.solve(np.kron(M, Dm) + np.kron(Dm, M), F1.ravel()).reshape(n, n)  # (3.6), dense
     assert _relmax(X[0], Xd) <= TOL_FP64
     assert _relmax(X[1], Xexact) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 33, 64, 257, 4096])
+def test_square_fp64_tight_spectrum_matches_oracle(api, n):
+    """FPS_TIGHT_SPECTRUM: shifts from the Sturm-bisection interval on both sides (the
+    library's and the oracle's own bisection), same J, parity at the FP64 bar."""
+    F = inputs.square_rhs(n, 40 + n)
+    plan = api.plan_create(n, 2, 1e-13, "fp64_tight")
+    X = api.poisson_square_solve(plan, torch.from_numpy(F).cuda()).cpu().numpy()
+    info = api.plan_info(plan)
+    q = api.plan_shifts(plan)
+    api.plan_destroy(plan)
+    lo, hi = oracle.tight_interval(n)
+    J = oracle.adi_iterations(-hi, -lo, lo, hi, 1e-13)
+    assert info["J"] == J == len(q)
+    _, qo = oracle.adi_shifts(-hi, -lo, lo, hi, 1e-13, J)
+    assert np.abs(np.sort(q) - np.sort(qo)).max() <= 1e-9 * np.abs(qo).max()
+    assert _relmax(X, oracle.poisson_square(F, 1e-13, tight=True)) <= TOL_FP64
+
+
+def test_square_fp64_tight_spectrum_full_size_10000(api):
+    F = inputs.square_rhs(10000, 3, power=1)
+    plan = api.plan_create(10000, 2, 1e-13, "fp64_tight")
+    X = api.poisson_square_solve(plan, torch.from_numpy(F).cuda()).cpu().numpy()
+    info = api.plan_info(plan)
+    api.plan_destroy(plan)
+    assert info["J"] == 110
+    assert _relmax(X, oracle.poisson_square(F, 1e-13, tight=True)) <= TOL_FP64

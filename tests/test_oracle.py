@@ -367,3 +367,31 @@ def test_cube_spectral_convergence_fig51():
         errs.append(np.abs(X - Xe).max())
     assert errs[0] > 1e2 * errs[1] > 1e4 * errs[2]
     assert errs[2] < 1e-8
+
+
+# ------------------------------------------------- tight spectral interval (f1)
+@pytest.mark.parametrize("n", [1, 2, 3, 10, 64, 300])
+def test_tight_interval_contains_spectrum(n):
+    """The oracle's Sturm-bisection interval contains sigma(A~) (eigvalsh) with the
+    stated padding: lo = |lambda_max| / 2, hi = min(1, 1.01 |lambda_min|)."""
+    lo, hi = oracle.tight_interval(n)
+    d, e = oracle.square_bands(n)
+    lam = np.linalg.eigvalsh(_dense_from_bands(d, e))
+    small, big = -lam.max(), -lam.min()
+    assert lo <= small and hi >= big
+    assert abs(lo - 0.5 * small) <= 1e-9 * small
+    assert abs(hi - min(1.0, 1.01 * big)) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 10, 64, 300, 2048, 10000])
+def test_tight_interval_library_agrees_with_oracle(n):
+    """The library's own bisection (host helper) and the oracle's give the same interval
+    and therefore the same J of (2.9) (133 -> 110 at n = 10^4, tol 1e-13)."""
+    from paper_1710_11259_gb300 import api
+
+    a = oracle.tight_interval(n)
+    b = api.square_spectral_interval(n, True)
+    assert abs(a[0] - b[0]) <= 1e-9 * a[0] and abs(a[1] - b[1]) <= 1e-12 * a[1]
+    Ja = oracle.adi_iterations(-a[1], -a[0], a[0], a[1], 1e-13)
+    Jb = oracle.adi_iterations(-b[1], -b[0], b[0], b[1], 1e-13)
+    assert Ja == Jb <= oracle.square_iterations(n, 1e-13)
