@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "bulk.cuh"
+#include "device_info.h"
 #include "sweep.cuh"
 
 namespace fps {
@@ -551,9 +552,9 @@ struct TileView {
     const double *d, *e, *s;
     int bx, by;
 };
-__device__ __forceinline__ TileView tile_view(const TileArgs &t)
+__device__ __forceinline__ TileView tile_view(const TileArgs &t, int64_t idx = -1)
 {
-    const int4 q = t.tiles[blockIdx.x];
+    const int4 q = t.tiles[idx < 0 ? (int64_t)blockIdx.x : idx];
     const TileProb &p = t.probs[q.x >> 8];
     TileView v;
     v.prob = q.x >> 8;
@@ -569,6 +570,16 @@ __device__ __forceinline__ TileView tile_view(const TileArgs &t)
     v.bx = q.y * 32;
     v.by = q.z * 32;
     return v;
+}
+
+// The contiguous run of tiles of this CTA, for the reduction kernels (tiles are
+// ordered pair by pair, so a run meets each (problem, rhs) pair once: one atomic per
+// pair and CTA instead of one per tile).
+__device__ __forceinline__ void tile_run(int64_t ntiles, int64_t &t0, int64_t &t1)
+{
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    t0 = (int64_t)blockIdx.x * per;
+    t1 = t0 + per < ntiles ? t0 + per : ntiles;
 }
 
 // c_{J-1} at (i, k) rebuilt from the column pass's local result and its chain.
@@ -637,18 +648,30 @@ __device__ __forceinline__ void block_max_to(double local, unsigned long long *o
         for (int q = 0; q < (int)blockDim.y; ++q) bm = fmax(bm, wmax[q]);
         atomicMax(out, (unsigned long long)__double_as_longlong(bm));
     }
+    __syncthreads();  // wmax is reused by the next reduction
 }
 
 __global__ void __launch_bounds__(256) absmax_kernel(TileArgs t, const double *__restrict__ F,
                                                      unsigned long long *__restrict__ smax)
 {
-    const TileView v = tile_view(t);
+    int64_t t0, t1;
+    tile_run(t.ntiles, t0, t1);
     double local = 0.0;
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        const int i = v.by + r, k = v.bx + threadIdx.x;
-        if (i < v.n && k < v.n) local = flag_nonfinite(fabs(F[v.off64 + (int64_t)i * v.n + k] * v.s[i] * v.s[k]), local);
+    int cur = -1;
+    for (int64_t tt = t0; tt < t1; ++tt) {
+        const TileView v = tile_view(t, tt);
+        if (v.pair != cur) {
+            if (cur >= 0) block_max_to(local, smax + cur);
+            local = 0.0;
+            cur = v.pair;
+        }
+        for (int r = threadIdx.y; r < 32; r += 8) {
+            const int i = v.by + r, k = v.bx + threadIdx.x;
+            if (i < v.n && k < v.n)
+                local = flag_nonfinite(fabs(F[v.off64 + (int64_t)i * v.n + k] * v.s[i] * v.s[k]), local);
+        }
     }
-    block_max_to(local, smax + v.pair);
+    if (cur >= 0) block_max_to(local, smax + cur);
 }
 
 template <typename T>
@@ -681,48 +704,59 @@ __global__ void __launch_bounds__(256) residual_kernel(TileArgs t, const double 
                                                        const int *__restrict__ pair_active, int y_zero)
 {
     __shared__ double Ys[36][37];
-    const TileView v = tile_view(t);
-    const int n = v.n;
-    if (!pair_active[v.pair]) {
-        for (int r = threadIdx.y; r < 32; r += 8) {
-            const int i = v.by + r, k = v.bx + threadIdx.x;
-            if (i < n && k < n) Yout[v.off64 + (int64_t)i * n + k] = y_zero ? 0.0 : Y[v.off64 + (int64_t)i * n + k];
-        }
-        return;
-    }
-    const double sF = __longlong_as_double((long long)smax[v.pair]);
-    const double inv = sF > 0.0 ? 1.0 / sF : 0.0;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int r = ty; r < 36; r += 8) {
-        const int i = v.by - 2 + r;
-        for (int cc = tx; cc < 36; cc += 32) {
-            const int k = v.bx - 2 + cc;
-            double val = 0.0;
-            if (i >= 0 && i < n && k >= 0 && k < n) {
-                val = y_zero ? 0.0 : Y[v.off64 + (int64_t)i * n + k];
-                val = fma(sF, (double)D[v.offT + (int64_t)(i + 2) * v.ldp + k + 4], val);
-            }
-            Ys[r][cc] = val;
-        }
-    }
-    __syncthreads();
+    int64_t t0, t1;
+    tile_run(t.ntiles, t0, t1);
     double local = 0.0;
-    for (int r = ty; r < 32; r += 8) {
-        const int i = v.by + r, k = v.bx + tx;
-        if (i < n && k < n) {
-            const double y = Ys[r + 2][tx + 2];
-            double acc = Ft[v.off64 + (int64_t)i * n + k];
-            acc = fma(-(v.d[i] + v.d[k]), y, acc);
-            if (i >= 2) acc = fma(-v.e[i - 2], Ys[r][tx + 2], acc);
-            acc = fma(-v.e[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
-            if (k >= 2) acc = fma(-v.e[k - 2], Ys[r + 2][tx], acc);
-            acc = fma(-v.e[k], Ys[r + 2][tx + 4], acc);
-            Yout[v.off64 + (int64_t)i * n + k] = y;
-            local = flag_nonfinite(fabs(acc), local);
-            rho0[v.offT + (int64_t)(i + 2) * v.ldp + k + 4] = (float)(acc * inv);
+    int cur = -1;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int64_t tt = t0; tt < t1; ++tt) {
+        const TileView v = tile_view(t, tt);
+        const int n = v.n;
+        if (v.pair != cur) {
+            if (cur >= 0) block_max_to(local, rmax + cur);
+            local = 0.0;
+            cur = v.pair;
         }
+        if (!pair_active[v.pair]) {  // converged pair: carry its iterate over unchanged
+            for (int r = ty; r < 32; r += 8) {
+                const int i = v.by + r, k = v.bx + tx;
+                if (i < n && k < n) Yout[v.off64 + (int64_t)i * n + k] = y_zero ? 0.0 : Y[v.off64 + (int64_t)i * n + k];
+            }
+            continue;
+        }
+        const double sF = __longlong_as_double((long long)smax[v.pair]);
+        const double inv = sF > 0.0 ? 1.0 / sF : 0.0;
+        for (int r = ty; r < 36; r += 8) {
+            const int i = v.by - 2 + r;
+            for (int cc = tx; cc < 36; cc += 32) {
+                const int k = v.bx - 2 + cc;
+                double val = 0.0;
+                if (i >= 0 && i < n && k >= 0 && k < n) {
+                    val = y_zero ? 0.0 : Y[v.off64 + (int64_t)i * n + k];
+                    val = fma(sF, (double)D[v.offT + (int64_t)(i + 2) * v.ldp + k + 4], val);
+                }
+                Ys[r][cc] = val;
+            }
+        }
+        __syncthreads();
+        for (int r = ty; r < 32; r += 8) {
+            const int i = v.by + r, k = v.bx + tx;
+            if (i < n && k < n) {
+                const double y = Ys[r + 2][tx + 2];
+                double acc = Ft[v.off64 + (int64_t)i * n + k];
+                acc = fma(-(v.d[i] + v.d[k]), y, acc);
+                if (i >= 2) acc = fma(-v.e[i - 2], Ys[r][tx + 2], acc);
+                acc = fma(-v.e[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
+                if (k >= 2) acc = fma(-v.e[k - 2], Ys[r + 2][tx], acc);
+                acc = fma(-v.e[k], Ys[r + 2][tx + 4], acc);
+                Yout[v.off64 + (int64_t)i * n + k] = y;
+                local = flag_nonfinite(fabs(acc), local);
+                rho0[v.offT + (int64_t)(i + 2) * v.ldp + k + 4] = (float)(acc * inv);
+            }
+        }
+        __syncthreads();  // Ys is refilled by the next tile
     }
-    block_max_to(local, rmax + v.pair);
+    if (cur >= 0) block_max_to(local, rmax + cur);
 }
 
 __global__ void __launch_bounds__(256) scale_out_kernel(TileArgs t, const double *__restrict__ Y, double *__restrict__ X)
@@ -750,6 +784,13 @@ cudaError_t col_pass_S(const SwArgs<T> &a, int j, cudaStream_t st)
 {
     col_pass_kernel<T, S><<<(unsigned)a.nitems, kCT, ColGeom<T, S>::bytes, st>>>(a, j);
     return cudaGetLastError();
+}
+
+// CTAs of a reduction kernel: 8 per SM (all resident), at most one per tile.
+unsigned reduction_grid(int64_t ntiles)
+{
+    const int64_t g = 8 * (int64_t)current_sm_count();
+    return (unsigned)(ntiles < g ? (ntiles > 0 ? ntiles : 1) : g);
 }
 
 }  // namespace
@@ -829,7 +870,7 @@ cudaError_t launch_finalize_out(const TileArgs &t, const SwArgs<double> &a, doub
 
 cudaError_t launch_absmax(const TileArgs &t, const double *F, unsigned long long *smax, cudaStream_t st)
 {
-    absmax_kernel<<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, F, smax);
+    absmax_kernel<<<reduction_grid(t.ntiles), dim3(32, 8), 0, st>>>(t, F, smax);
     return cudaGetLastError();
 }
 
@@ -845,7 +886,7 @@ cudaError_t launch_residual(const TileArgs &t, const double *Y, double *Yout, co
                             float *rho0, const unsigned long long *smax, unsigned long long *rmax,
                             const int *pair_active, bool y_zero, cudaStream_t st)
 {
-    residual_kernel<<<(unsigned)t.ntiles, dim3(32, 8), 0, st>>>(t, Y, Yout, D, Ft, rho0, smax, rmax, pair_active,
+    residual_kernel<<<reduction_grid(t.ntiles), dim3(32, 8), 0, st>>>(t, Y, Yout, D, Ft, rho0, smax, rmax, pair_active,
                                                                y_zero ? 1 : 0);
     return cudaGetLastError();
 }

@@ -10,8 +10,9 @@
 //            stop (their iterate is carried unchanged).
 //   X = D_s Y D_s.
 // The inner tolerance of a round is the coarsest level that still gains ten times
-// what the worst active pair is missing; the first round uses the finest level
-// (1e-7, the accuracy an FP32 inner solve can deliver).  Inner shifts come from the
+// what the worst active pair is missing; the first round stops at the coarsest
+// level not above sqrt(0.1 tol), so that two rounds of equal gain reach tol (the
+// finest level, 1e-7, is about what one FP32 inner solve can deliver).  Inner shifts come from the
 // tight spectral interval of A~ (the refinement is judged by the FP64 residual).
 // FP64 (plain method): rho_0 = F~, one graph of J iterations of (2.9), then
 // X = D_s Y_J D_s fused with the last correction.
@@ -621,7 +622,14 @@ int SweepEngine<T>::solve_refine(const double *F, double *X, cudaStream_t st, st
             size_t li = 0;
             for (size_t l = 0; l < levels_.size(); ++l)
                 if (levels_[l].tol <= want) li = l;
-            if (round == 0) li = 0;
+            if (round == 0) {
+                // two balanced rounds: the first stops near sqrt(0.1 tol), which leaves the
+                // second a gain of the same size (1e-6 then 1e-5 for tol = 1e-10)
+                const double first = std::sqrt(0.1 * tol_);
+                li = 0;
+                for (size_t l = 0; l < levels_.size(); ++l)
+                    if (levels_[l].tol <= first) li = l;
+            }
             ENG_CK(cudaGraphLaunch(levels_[li].graph, st));
             levels_used_.push_back((int)li);
             launches_last += 4LL * levels_[li].Jmax + 1;

