@@ -75,6 +75,9 @@ def _lib(variant: str = "double") -> ctypes.CDLL:
             lib.orc_poisson_square_tight.argtypes = [ctypes.c_long, ctypes.c_double, c_dp, c_dp]
             lib.orc_poisson_square_tight.restype = ctypes.c_int
             lib.orc_tight_interval.argtypes = [ctypes.c_long, c_dp, c_dp]
+            lib.orc_poisson_rectangle.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_int, c_dp, c_dp]
+            lib.orc_poisson_rectangle.restype = ctypes.c_int
             lib.orc_poisson_square_partial.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_int, c_dp, c_dp]
             lib.orc_poisson_square_partial.restype = ctypes.c_int
             lib.orc_poisson_cube.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double, c_dp,
@@ -168,6 +171,25 @@ def poisson_square(F, tol: float = 1e-13, variant: str = "double", tight: bool =
     else:
         _lib(variant).orc_poisson_square(n, tol, _ptr(F), _ptr(X))
     return X
+
+
+def rect_scales(width: float, height: float):
+    """(kx, ky) = ((2/width)^2, (2/height)^2): the factors the affine map of
+    [x0, x0 + width] x [y0, y0 + height] onto [-1, 1]^2 puts on u_xx and u_yy."""
+    return (2.0 / width) ** 2, (2.0 / height) ** 2
+
+
+def poisson_rectangle(F, width: float, height: float, tol: float = 1e-13, variant: str = "double",
+                      tight: bool = False):
+    """Poisson on a width x height rectangle, homogeneous Dirichlet data:
+    kx M X D^T + ky D X M^T = F, F and X in the mapped C~ basis (X_ij pairs C~_i(y)
+    with C~_j(x)).  Returns (X, J)."""
+    F = _f64(F)
+    n = F.shape[0]
+    X = np.zeros_like(F)
+    kx, ky = rect_scales(width, height)
+    J = _lib(variant).orc_poisson_rectangle(n, kx, ky, tol, 1 if tight else 0, _ptr(F), _ptr(X))
+    return X, int(J)
 
 
 def tight_interval(n: int):

@@ -76,6 +76,23 @@ def poly_eval(c: np.ndarray, X: np.ndarray, Y: np.ndarray) -> np.ndarray:
     return P.polyval2d(X, Y, c)
 
 
+def manufactured_rectangle(pc: np.ndarray, n: int, kx: float, ky: float):
+    """As manufactured_square on the mapped rectangle: u = (1-s^2)(1-t^2) p(s,t) in the
+    coordinates s (x) and t (y) of [-1,1]^2, and f = kx u_ss + ky u_tt, the Laplacian
+    of u on a rectangle whose side lengths are 2/sqrt(kx) and 2/sqrt(ky)."""
+    u = poly_times_bubble(pc)
+    uxx = P.polyder(u, 2, axis=0)
+    uyy = P.polyder(u, 2, axis=1)
+    f = np.zeros(u.shape)
+    f[: uxx.shape[0], : uxx.shape[1]] += kx * uxx
+    f[: uyy.shape[0], : uyy.shape[1]] += ky * uyy
+    deg = u.shape[0] + u.shape[1]
+    N = n + deg + 4
+    F = project_2d(lambda X, Y: poly_eval(f, X, Y), n, N)
+    Xe = project_2d(lambda X, Y: poly_eval(pc, X, Y), n, N)
+    return F, Xe
+
+
 def manufactured_square(pc: np.ndarray, n: int):
     """Manufactured pair for eq. (3.1): u = (1-x^2)(1-y^2) p(x,y).
 

@@ -455,15 +455,18 @@ void orc_tight_interval(long n, double *lo, double *hi)
 /*   6. X = D_s Y D_s                                            (reading R2)  */
 /* F, X: n x n row-major, X_ij pairs C~_i(y) with C~_j(x).  Returns J.         */
 /* ------------------------------------------------------------------------- */
-static int poisson_square(long n, double tol, const real *F, real *X, double *shifts_q_out, int jmax, int tight)
+static int poisson_square(long n, double tol, const real *F, real *X, double *shifts_q_out, int jmax, int tight,
+                          double kx, double ky)
 {
     size_t nn = (size_t)n * (size_t)n;
     long ne = n > 2 ? n - 2 : 1;
     real *ad = malloc(sizeof(real) * (size_t)n), *ae = malloc(sizeof(real) * (size_t)ne);
     real *bd = malloc(sizeof(real) * (size_t)n), *be = malloc(sizeof(real) * (size_t)ne);
     square_bands(n, ad, ae);
-    for (long j = 0; j < n; ++j) bd[j] = -ad[j];
-    for (long j = 0; j + 2 < n; ++j) be[j] = -ae[j];
+    /* rectangle (Sec. 3 on [x0,x1] x [y0,y1]): kx A~ Y + ky Y A~ = F~ with k = (2/length)^2;
+     * A = kx A~ acts on the row (y) index, B = -ky A~ on the column (x) index */
+    for (long j = 0; j < n; ++j) { bd[j] = -ky * ad[j]; ad[j] *= kx; }
+    for (long j = 0; j + 2 < n; ++j) { be[j] = -ky * ae[j]; ae[j] *= kx; }
 
     real *Ft = malloc(sizeof(real) * nn), *Y = malloc(sizeof(real) * nn);
     for (long i = 0; i < n; ++i)
@@ -483,6 +486,10 @@ static int poisson_square(long n, double tol, const real *F, real *X, double *sh
         c = tlo;
         d = thi;
     }
+    a *= kx;
+    b *= kx;
+    c *= ky;
+    d *= ky;
     int J = orc_adi_iterations(a, b, c, d, tol);
     double *p = malloc(sizeof(double) * (size_t)J), *q = malloc(sizeof(double) * (size_t)J);
     orc_adi_shifts(a, b, c, d, tol, J, p, q);
@@ -506,7 +513,24 @@ int orc_poisson_square(long n, double tol, const double *F, double *X)
     size_t nn = (size_t)n * (size_t)n;
     real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
     for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
-    int J = poisson_square(n, tol, Fr, Xr, NULL, 0, 0);
+    int J = poisson_square(n, tol, Fr, Xr, NULL, 0, 0, 1.0, 1.0);
+    for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
+    free(Fr);
+    free(Xr);
+    return J;
+}
+
+/* Poisson on the rectangle [x0, x1] x [y0, y1] with homogeneous Dirichlet data: the
+ * affine map to [-1,1]^2 scales the second derivatives by kx = (2/(x1-x0))^2 and
+ * ky = (2/(y1-y0))^2, so (3.6) becomes kx M X D^T + ky D X M^T = F; in the variables
+ * of (3.9), kx A~ Y + ky Y A~ = F~, a Sylvester equation whose two spectral intervals
+ * differ (non-symmetric shifts from App. A's general Moebius path). */
+int orc_poisson_rectangle(long n, double kx, double ky, double tol, int tight, const double *F, double *X)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
+    for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
+    int J = poisson_square(n, tol, Fr, Xr, NULL, 0, tight, kx, ky);
     for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
     free(Fr);
     free(Xr);
@@ -519,7 +543,7 @@ int orc_poisson_square_tight(long n, double tol, const double *F, double *X)
     size_t nn = (size_t)n * (size_t)n;
     real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
     for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
-    int J = poisson_square(n, tol, Fr, Xr, NULL, 0, 1);
+    int J = poisson_square(n, tol, Fr, Xr, NULL, 0, 1, 1.0, 1.0);
     for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
     free(Fr);
     free(Xr);
@@ -534,7 +558,7 @@ int orc_poisson_square_partial(long n, double tol, int jmax, const double *F, do
     size_t nn = (size_t)n * (size_t)n;
     real *Fr = malloc(sizeof(real) * nn), *Xr = malloc(sizeof(real) * nn);
     for (size_t t = 0; t < nn; ++t) Fr[t] = F[t];
-    int J = poisson_square(n, tol, Fr, Xr, NULL, jmax, 0);
+    int J = poisson_square(n, tol, Fr, Xr, NULL, jmax, 0, 1.0, 1.0);
     for (size_t t = 0; t < nn; ++t) X[t] = (double)Xr[t];
     free(Fr);
     free(Xr);

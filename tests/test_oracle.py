@@ -418,3 +418,35 @@ def test_tight_interval_shifts_against_mpmath(n):
     rel = lambda a: float(np.max(np.abs(np.sort(a) - np.sort(exact)) / np.sort(exact)))
     assert rel(ql) <= 1e-10
     assert rel(qo) <= 2e-6
+
+
+# ------------------------------------------------------------ rectangle (f2)
+@pytest.mark.parametrize("n,w,h", [(3, 2.0, 0.5), (8, 1.0, 3.0), (17, 5.0, 2.0)])
+def test_rectangle_dense_kronecker(n, w, h):
+    """kx M X D^T + ky D X M^T = F (the rectangle form of (3.6)) solved densely."""
+    kx, ky = oracle.rect_scales(w, h)
+    d, e = oracle.M_bands(n)
+    M = _dense_from_bands(d, e)
+    Dm = np.diag([-(j + 1.0) * (j + 2.0) for j in range(n)])
+    F = inputs.square_rhs(n, 5)
+    L = kx * np.kron(M, Dm) + ky * np.kron(Dm, M)
+    Xd = np.linalg.solve(L, F.ravel()).reshape(n, n)
+    X, J = oracle.poisson_rectangle(F, w, h, 1e-13)
+    assert _relmax(X, Xd) < 2e-13
+    assert J > 0
+
+
+def test_rectangle_reduces_to_square():
+    F = inputs.square_rhs(40, 6)
+    X, _ = oracle.poisson_rectangle(F, 2.0, 2.0, 1e-13)
+    assert np.array_equal(X, oracle.poisson_square(F, 1e-13))
+
+
+@pytest.mark.parametrize("w,h", [(2.0, 0.5), (6.0, 1.5)])
+def test_rectangle_manufactured(w, h):
+    """u = (1-s^2)(1-t^2) p(s,t) on a w x h rectangle (deg p = 10): coefficients recovered."""
+    kx, ky = oracle.rect_scales(w, h)
+    pc = basis.monomial_coeffs(inputs.poly_values(1), 10)
+    F, Xe = basis.manufactured_rectangle(pc, 32, kx, ky)
+    X, _ = oracle.poisson_rectangle(F, w, h, 1e-13)
+    assert _relmax(X, Xe) < 5e-13
