@@ -110,6 +110,23 @@ typedef struct {
 int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precision, int nrhs, void *stream);
 
 /*
+ * fps_plan_create_rect -- plan Poisson's equation on the rectangle [x0, x0 + width] x
+ * [y0, y0 + height] with homogeneous Dirichlet data (Sec. 3 on a rectangle).  The
+ * affine map onto [-1,1]^2 multiplies u_xx by kx = (2/width)^2 and u_yy by
+ * ky = (2/height)^2, so the discrete equation is kx M X D^T + ky D X M^T = F in the
+ * mapped C~ coefficients (X[i*n + j] pairs C~_i(y) with C~_j(x)); in the variables of
+ * (3.9) it is kx A~ Y + ky Y A~ = F~, a Sylvester equation whose two spectral
+ * intervals differ, solved by Algorithm 2 with the general shifts of App. A.  Solve
+ * with fps_poisson_square_solve (the adjoint is the same solve: the map stays
+ * self-adjoint).  fps_plan_shifts returns the column-side shifts q_j.
+ *   width, height  side lengths, positive and finite (only they matter, not x0, y0).
+ *   others         as fps_plan_create for dim = 2 (precision may carry FPS_TIGHT_SPECTRUM).
+ * Errors as fps_plan_create.
+ */
+int fps_plan_create_rect(fps_plan **out, int64_t n, double width, double height, double tol, int precision,
+                         int nrhs, void *stream);
+
+/*
  * fps_plan_create_batched -- plan `count` independent squares of sizes ns[0..count-1]
  * (each with its own J and shifts), each with `nrhs` right-hand sides.  Layout
  * of F and X: problem after problem, each problem's nrhs n_p x n_p matrices back

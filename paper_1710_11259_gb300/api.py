@@ -69,7 +69,7 @@ EXPORTED = [
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
     "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
     "fps_square_spectral_interval", "fps_legendre_to_ctilde", "fps_solution_to_legendre", "fps_plan_pass_times",
-    "fps_probe_fma_rate",
+    "fps_probe_fma_rate", "fps_plan_create_rect",
 ]
 
 
@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
         L.fps_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
         L.fps_plan_pass_times.argtypes = [vp, dp, dp]
         L.fps_probe_fma_rate.argtypes = [ctypes.c_int, dp]
+        L.fps_plan_create_rect.argtypes = [ctypes.POINTER(vp), i64, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, vp]
         L.fps_poisson_square_solve_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp]
         L.fps_square_spectral_interval.argtypes = [i64, ctypes.c_int, dp, dp]
         L.fps_legendre_to_ctilde.argtypes = [i64, vp, vp, vp]
@@ -192,6 +194,17 @@ def plan_create(n: int, dim: int = 2, tol: float = 1e-13, precision="fp64", nrhs
     _check(lib().fps_plan_create(ctypes.byref(h), int(n), int(dim), float(tol), _PRECISION[precision], int(nrhs),
                                  ctypes.c_void_p(s)))
     return Plan(h.value, int(n), int(dim), int(nrhs))
+
+
+def plan_create_rect(n: int, width: float, height: float, tol: float = 1e-13, precision="fp64", nrhs: int = 1,
+                     stream: Optional[int] = None) -> Plan:
+    """Plan on a width x height rectangle (homogeneous Dirichlet); solve with
+    poisson_square_solve."""
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else int(stream)
+    _check(lib().fps_plan_create_rect(ctypes.byref(h), int(n), float(width), float(height), float(tol),
+                                      _PRECISION[precision], int(nrhs), ctypes.c_void_p(s)))
+    return Plan(h.value, int(n), 2, int(nrhs))
 
 
 def plan_create_batched(ns, nrhs: int = 1, tol: float = 1e-10, precision="fp32_refine",

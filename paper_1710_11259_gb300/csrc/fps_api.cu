@@ -93,6 +93,7 @@ struct fps_plan {
 
     bool instrument = false;
     int64_t launches_last = 0;
+    double kx = 1.0, ky = 1.0;  // scales of u_xx and u_yy (rectangle plans)
 };
 
 namespace {
@@ -208,6 +209,88 @@ int solve_square(fps_plan *p, const double *F, double *X, const char *what)
     return solve_engine(p, p->eng64, F, X, fdev, xdev, what);
 }
 
+// A square (kx = ky = 1) or rectangle plan: kx A~ Y + ky Y A~ = F~.
+int create_square(fps_plan **out, int64_t n, double tol, int precision, bool tight, int nrhs, void *stream,
+                  double kx, double ky, const char *what)
+{
+    fps_plan *p = new fps_plan();
+    p->n = n;
+    p->dim = 2;
+    p->tol = tol;
+    p->precision = precision;
+    p->nrhs = nrhs;
+    p->kx = kx;
+    p->ky = ky;
+    p->stream = (cudaStream_t)stream;
+    p->total_elems = n * n * nrhs;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return fail(FPS_ERR_CUDA, std::string(what) + ": no CUDA device");
+    }
+    auto bail = [&](int s) {
+        release(p);
+        return s;
+    };
+#define PCK(call)                                                                                        \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return bail(fail(FPS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)));          \
+    } while (0)
+
+    // Lemma B.2 interval (or the tight one) of A~, scaled to the intervals of kx A~ and
+    // -ky A~; (2.9) J; (2.4) shifts (on a square p_j = -q_j; the q_j are kept for info)
+    const bool square = kx == ky;
+    double lo = fps::square_eps(n), hi = 1.0;
+    if (tight && precision == FPS_FP64) fps::square_tight_interval(n, lo, hi);
+    p->J = fps::adi_iterations(-kx * hi, -kx * lo, ky * lo, ky * hi, tol);
+    if (square) {
+        fps::zolotarev_shifts_symmetric(lo, hi, p->J, p->q);
+        for (double &v : p->q) v *= kx;
+    } else {
+        std::vector<double> pp;
+        fps::zolotarev_shifts(-kx * hi, -kx * lo, ky * lo, ky * hi, p->J, pp, p->q);
+    }
+    if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, std::string(what) + ": squares support n <= 40000"));
+    if (nrhs > 256) return bail(fail(FPS_ERR_UNSUPPORTED, std::string(what) + ": squares support nrhs <= 256"));
+    PCK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    std::string err;
+    int st;
+    if (precision == FPS_FP64 && n <= fps::kSmallMaxN && kx == 1.0 && ky == 1.0) {
+        // whole ADI in one launch: bands, shifts and reduction coefficients on the device
+        std::vector<double> d, e, s, pcr;
+        fps::square_bands(n, d, e);
+        fps::inv_sqrt_E(n, s);
+        fps::small_pcr_coefficients(n, d, e, p->q, pcr);
+        std::vector<double> bands(3 * n);
+        std::copy(d.begin(), d.end(), bands.begin());
+        std::copy(e.begin(), e.end(), bands.begin() + n);
+        std::copy(s.begin(), s.end(), bands.begin() + 2 * n);
+        PCK(fps::small_setup_kernel());
+        PCK(cudaMalloc((void **)&p->sm_bands, sizeof(double) * 3 * n));
+        PCK(cudaMalloc((void **)&p->sm_q, sizeof(double) * p->J));
+        PCK(cudaMalloc((void **)&p->sm_pcr, sizeof(double) * pcr.size()));
+        PCK(cudaMemcpy(p->sm_bands, bands.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+        PCK(cudaMemcpy(p->sm_q, p->q.data(), sizeof(double) * p->J, cudaMemcpyHostToDevice));
+        PCK(cudaMemcpy(p->sm_pcr, pcr.data(), sizeof(double) * pcr.size(), cudaMemcpyHostToDevice));
+        p->bytes += (int64_t)sizeof(double) * (3 * n + p->J + (int64_t)pcr.size());
+        p->small = true;
+        st = FPS_OK;
+    } else if (precision == FPS_FP64) {
+        p->eng64 = new fps::SweepEngine<double>();
+        st = p->eng64->create(std::vector<int64_t>{n}, nrhs, tol, tight, p->cap_stream, err, 0, kx, ky);
+        if (st == FPS_OK) p->bytes += p->eng64->bytes;
+    } else {
+        p->eng32 = new fps::SweepEngine<float>();
+        st = p->eng32->create(std::vector<int64_t>{n}, nrhs, tol, true, p->cap_stream, err, 0, kx, ky);
+        if (st == FPS_OK) p->bytes += p->eng32->bytes;
+    }
+    if (st != FPS_OK) return bail(fail(st, std::string(what) + ": " + err));
+#undef PCK
+    *out = p;
+    return FPS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -253,73 +336,26 @@ int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precisio
         return FPS_OK;
     }
 
-    fps_plan *p = new fps_plan();
-    p->n = n;
-    p->dim = dim;
-    p->tol = tol;
-    p->precision = precision;
-    p->nrhs = nrhs;
-    p->stream = (cudaStream_t)stream;
-    p->total_elems = n * n * nrhs;
-    if (cudaGetDevice(&p->device) != cudaSuccess) {
-        delete p;
-        return fail(FPS_ERR_CUDA, "fps_plan_create: no CUDA device");
-    }
-    auto bail = [&](int s) {
-        release(p);
-        return s;
-    };
-#define PCK(call)                                                                                        \
-    do {                                                                                                 \
-        cudaError_t e_ = (call);                                                                         \
-        if (e_ != cudaSuccess)                                                                           \
-            return bail(fail(FPS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)));          \
-    } while (0)
+    return create_square(out, n, tol, precision, tight, nrhs, stream, 1.0, 1.0, "fps_plan_create");
+}
 
-    // Lemma B.2 interval (or the tight one), (2.9) J, (2.4) shifts (symmetric
-    // intervals: p_j = -q_j).
-    double lo = fps::square_eps(n), hi = 1.0;
-    if (tight && precision == FPS_FP64) fps::square_tight_interval(n, lo, hi);
-    p->J = fps::adi_iterations(-hi, -lo, lo, hi, tol);
-    fps::zolotarev_shifts_symmetric(lo, hi, p->J, p->q);
-    if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the square supports n <= 40000"));
-    if (nrhs > 256) return bail(fail(FPS_ERR_UNSUPPORTED, "fps_plan_create: the square supports nrhs <= 256"));
-    PCK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
-    std::string err;
-    int st;
-    if (precision == FPS_FP64 && n <= fps::kSmallMaxN) {
-        // whole ADI in one launch: bands, shifts and reduction coefficients on the device
-        std::vector<double> d, e, s, pcr;
-        fps::square_bands(n, d, e);
-        fps::inv_sqrt_E(n, s);
-        fps::small_pcr_coefficients(n, d, e, p->q, pcr);
-        std::vector<double> bands(3 * n);
-        std::copy(d.begin(), d.end(), bands.begin());
-        std::copy(e.begin(), e.end(), bands.begin() + n);
-        std::copy(s.begin(), s.end(), bands.begin() + 2 * n);
-        PCK(fps::small_setup_kernel());
-        PCK(cudaMalloc((void **)&p->sm_bands, sizeof(double) * 3 * n));
-        PCK(cudaMalloc((void **)&p->sm_q, sizeof(double) * p->J));
-        PCK(cudaMalloc((void **)&p->sm_pcr, sizeof(double) * pcr.size()));
-        PCK(cudaMemcpy(p->sm_bands, bands.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
-        PCK(cudaMemcpy(p->sm_q, p->q.data(), sizeof(double) * p->J, cudaMemcpyHostToDevice));
-        PCK(cudaMemcpy(p->sm_pcr, pcr.data(), sizeof(double) * pcr.size(), cudaMemcpyHostToDevice));
-        p->bytes += (int64_t)sizeof(double) * (3 * n + p->J + (int64_t)pcr.size());
-        p->small = true;
-        st = FPS_OK;
-    } else if (precision == FPS_FP64) {
-        p->eng64 = new fps::SweepEngine<double>();
-        st = p->eng64->create(std::vector<int64_t>{n}, nrhs, tol, tight, p->cap_stream, err);
-        if (st == FPS_OK) p->bytes += p->eng64->bytes;
-    } else {
-        p->eng32 = new fps::SweepEngine<float>();
-        st = p->eng32->create(std::vector<int64_t>{n}, nrhs, tol, true, p->cap_stream, err);
-        if (st == FPS_OK) p->bytes += p->eng32->bytes;
-    }
-    if (st != FPS_OK) return bail(fail(st, "fps_plan_create: " + err));
-#undef PCK
-    *out = p;
-    return FPS_OK;
+int fps_plan_create_rect(fps_plan **out, int64_t n, double width, double height, double tol, int precision,
+                         int nrhs, void *stream)
+{
+    fps::TraceRange tr("fps_plan_create_rect");
+    if (!out) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_rect: out is NULL");
+    *out = nullptr;
+    if (n < 1) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_rect: n must be >= 1");
+    if (!(width > 0.0 && height > 0.0 && std::isfinite(width) && std::isfinite(height)))
+        return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_rect: width and height must be positive and finite");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_rect: tol must lie in (0, 1)");
+    if (nrhs < 1) return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_rect: nrhs must be >= 1");
+    const bool tight = (precision & FPS_TIGHT_SPECTRUM) != 0;
+    precision &= ~FPS_TIGHT_SPECTRUM;
+    if (precision != FPS_FP64 && precision != FPS_FP32_REFINE)
+        return fail(FPS_ERR_INVALID_ARG, "fps_plan_create_rect: unknown precision");
+    const double kx = (2.0 / width) * (2.0 / width), ky = (2.0 / height) * (2.0 / height);
+    return create_square(out, n, tol, precision, tight, nrhs, stream, kx, ky, "fps_plan_create_rect");
 }
 
 int fps_plan_create_batched(fps_plan **out, const int64_t *ns, int64_t count, int nrhs, double tol, int precision,

@@ -206,9 +206,11 @@ __device__ __forceinline__ void row_pass_tile(const SwArgs<T> &a, int j, const i
     T *Dp = a.D + base;
     T *alp = a.al + base;
     const int64_t sbase = pr.soff + (int64_t)it.y * pr.srhs;
-    const Fac<T> *facj = pr.fac + (int64_t)j * (N + 4);
-    const Fac<T> *facp = pr.fac + (int64_t)(MODE > 0 ? j - 1 : 0) * (N + 4);
-    const T qprev = MODE > 0 ? pr.q[j - 1] : T(0);
+    const Fac<T> *facj = pr.facR + (int64_t)j * (N + 4);                      // this row solve
+    const Fac<T> *facp = pr.facC + (int64_t)(MODE > 0 ? j - 1 : 0) * (N + 4);  // previous column solve
+    const T sL = MODE > 0 ? pr.sh[3 * (j - 1)] : T(0);      // column-stencil shift of iteration j-1
+    const T sR = MODE > 0 ? pr.sh[3 * (j - 1) + 1] : T(0);  // row-stencil shift
+    const T fD = MODE > 0 ? pr.sh[3 * (j - 1) + 2] : T(0);  // correction factor
 
     // column segments of the halo rows (row systems of the previous column pass)
     const int sc = i0 / S, segstart = sc * S, segend = min(segstart + S, N);
@@ -268,7 +270,7 @@ __device__ __forceinline__ void row_pass_tile(const SwArgs<T> &a, int j, const i
         const T ipk = fcol[c].ip;
         if (MODE > 0) {
             cf[4 * c + 0] = ipk * pr.e[k];
-            cf[4 * c + 1] = ipk * (pr.d[k + 2] + qprev);
+            cf[4 * c + 1] = ipk * (pr.d[k + 2] + sR);
             cf[4 * c + 2] = ipk * pr.e[k + 2];
         } else {
             cf[4 * c + 0] = T(0);
@@ -301,14 +303,14 @@ __device__ __forceinline__ void row_pass_tile(const SwArgs<T> &a, int j, const i
         }
         __syncthreads();
         // D -= 2 q_{j-1} c_{j-1} on the core (D = -2 q_0 c_0 at j = 1)
-        const T q2 = T(2) * qprev;
+
 #pragma unroll
         for (int m = 0; m < NDC; ++m) {
             const int rr = dr0 + m * DSTEP;
             T v[V], dv[V];
             ld16(ct + (rr + 2) * SW + 4 + dc * V, v);
 #pragma unroll
-            for (int e = 0; e < V; ++e) dv[e] = MODE == 1 ? -q2 * v[e] : fma(-q2, v[e], dreg[m][e]);
+            for (int e = 0; e < V; ++e) dv[e] = MODE == 1 ? fD * v[e] : fma(fD, v[e], dreg[m][e]);
             st16(Dp + (int64_t)(i0 + rr + 2) * ldp + (k0 + 4 + dc * V), dv);
         }
     }
@@ -332,7 +334,7 @@ __device__ __forceinline__ void row_pass_tile(const SwArgs<T> &a, int j, const i
             }
         } else {
             // rho = ip (R + q)(L + q) c: column stencil u = (L + q) c, then the row stencil
-            const T eu = pr.e[i], dq = pr.d[i + 2] + qprev, ed = pr.e[i + 2];
+            const T eu = pr.e[i], dq = pr.d[i + 2] + sL, ed = pr.e[i + 2];
             const T *r0 = ct + (r - 2) * SW + 4, *r1 = ct + r * SW + 4, *r2 = ct + (r + 2) * SW + 4;
             auto u = [&](int x) { return fma(eu, r0[x], fma(dq, r1[x], ed * r2[x])); };
             T um = u(p - 2), u0 = u(p);
@@ -406,7 +408,8 @@ __device__ __forceinline__ void col_pass_tile(const SwArgs<T> &a, int j, const i
     const int cs = k0 / S;  // row-system segment holding these columns
     const int64_t base = pr.off + (int64_t)it.y * pr.rhs;
     const int64_t sbase = pr.soff + (int64_t)it.y * pr.srhs;
-    const Fac<T> *facj = pr.fac + (int64_t)j * (N + 4);
+    const Fac<T> *facj = pr.facC + (int64_t)j * (N + 4);  // this column solve
+    const Fac<T> *facr = pr.facR + (int64_t)j * (N + 4);  // the row solve whose result is rebuilt
 
     if (tid == 0) {
         bulk::mbar_init(bar, 1);
@@ -427,7 +430,7 @@ __device__ __forceinline__ void col_pass_tile(const SwArgs<T> &a, int j, const i
     // one thread per (column, parity of the row index)
     const int kk = tid % kC, p = tid / kC;
     const int k = k0 + kk;
-    const T bv = facj[k + 2].Bv, ps = facj[k + 2].Psi;
+    const T bv = facr[k + 2].Bv, ps = facr[k + 2].Psi;
     const T2 *zp = zx + (k & 1) * G::ZS;
     if (!tile_ready(bar, a.err)) return;
 
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(2 * kChainLines) chain_kernel(SwArgs<T> a, int
     T2 *__restrict__ zx = (dir == 0 ? a.zxR : a.zxC) + sbase + p * (N + 8) + l + 4;
     T *__restrict__ zs = a.zin + sbase + p * (N + 8) + l + 4;
     const int64_t step = 2 * (int64_t)(N + 8);  // next segment, same parity and line
-    const Fac<T> *__restrict__ facj = pr.fac + (int64_t)j * (N + 4) + 2;
+    const Fac<T> *__restrict__ facj = (dir == 0 ? pr.facR : pr.facC) + (int64_t)j * (N + 4) + 2;
     T W = 0;
     for (int s0 = 0; s0 < P; s0 += B) {
         T sx[B], ph[B];
@@ -550,6 +553,7 @@ struct TileView {
     int n, ldp, prob, rhs, pair;
     int64_t off64, offT;
     const double *d, *e, *s;
+    double kx, ky;
     int bx, by;
 };
 __device__ __forceinline__ TileView tile_view(const TileArgs &t, int64_t idx = -1)
@@ -567,6 +571,8 @@ __device__ __forceinline__ TileView tile_view(const TileArgs &t, int64_t idx = -
     v.e = p.e;
     v.s = p.s;
     v.pair = p.pair0 + v.rhs;
+    v.kx = p.kx;
+    v.ky = p.ky;
     v.bx = q.y * 32;
     v.by = q.z * 32;
     return v;
@@ -599,15 +605,15 @@ __global__ void __launch_bounds__(256) finalize_kernel(TileArgs t, SwArgs<T> a, 
     if (!pair_active[v.pair]) return;
     const SwProb<T> &pr = a.probs[v.prob];
     const int J = pr.J;
-    const T q2 = T(2) * pr.q[J - 1];
-    const Fac<T> *fac = pr.fac + (int64_t)(J - 1) * (pr.N + 4) + 2;
+    const T fD = pr.sh[3 * (J - 1) + 2];
+    const Fac<T> *fac = pr.facC + (int64_t)(J - 1) * (pr.N + 4) + 2;
     const int64_t sbase = pr.soff + (int64_t)v.rhs * pr.srhs;
     for (int r = threadIdx.y; r < 32; r += 8) {
         const int i = v.by + r, k = v.bx + threadIdx.x;
         if (i < v.n && k < v.n) {
             const T c = rebuilt_c(a, pr, v.offT, sbase, fac[i], i, k);
             T *dp = a.D + v.offT + (int64_t)(i + 2) * pr.ldp + k + 4;
-            *dp = (J >= 2) ? fma(-q2, c, *dp) : -q2 * c;
+            *dp = (J >= 2) ? fma(fD, c, *dp) : fD * c;
         }
     }
 }
@@ -618,14 +624,14 @@ __global__ void __launch_bounds__(256) finalize_out_kernel(TileArgs t, SwArgs<do
     const SwProb<double> &pr = a.probs[v.prob];
     if (!a.active[v.prob]) return;
     const int J = pr.J;
-    const double q2 = 2.0 * pr.q[J - 1];
-    const Fac<double> *fac = pr.fac + (int64_t)(J - 1) * (pr.N + 4) + 2;
+    const double fD = pr.sh[3 * (J - 1) + 2];
+    const Fac<double> *fac = pr.facC + (int64_t)(J - 1) * (pr.N + 4) + 2;
     const int64_t sbase = pr.soff + (int64_t)v.rhs * pr.srhs;
     for (int r = threadIdx.y; r < 32; r += 8) {
         const int i = v.by + r, k = v.bx + threadIdx.x;
         if (i < v.n && k < v.n) {
             const double c = rebuilt_c(a, pr, v.offT, sbase, fac[i], i, k);
-            const double y = (J >= 2) ? fma(-q2, c, a.D[v.offT + (int64_t)(i + 2) * pr.ldp + k + 4]) : -q2 * c;
+            const double y = (J >= 2) ? fma(fD, c, a.D[v.offT + (int64_t)(i + 2) * pr.ldp + k + 4]) : fD * c;
             X[v.off64 + (int64_t)i * v.n + k] = y * v.s[i] * v.s[k];
         }
     }
@@ -744,11 +750,11 @@ __global__ void __launch_bounds__(256) residual_kernel(TileArgs t, const double 
             if (i < n && k < n) {
                 const double y = Ys[r + 2][tx + 2];
                 double acc = Ft[v.off64 + (int64_t)i * n + k];
-                acc = fma(-(v.d[i] + v.d[k]), y, acc);
-                if (i >= 2) acc = fma(-v.e[i - 2], Ys[r][tx + 2], acc);
-                acc = fma(-v.e[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
-                if (k >= 2) acc = fma(-v.e[k - 2], Ys[r + 2][tx], acc);
-                acc = fma(-v.e[k], Ys[r + 2][tx + 4], acc);
+                acc = fma(-(v.kx * v.d[i] + v.ky * v.d[k]), y, acc);
+                if (i >= 2) acc = fma(-v.kx * v.e[i - 2], Ys[r][tx + 2], acc);
+                acc = fma(-v.kx * v.e[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
+                if (k >= 2) acc = fma(-v.ky * v.e[k - 2], Ys[r + 2][tx], acc);
+                acc = fma(-v.ky * v.e[k], Ys[r + 2][tx + 4], acc);
                 Yout[v.off64 + (int64_t)i * n + k] = y;
                 local = flag_nonfinite(fabs(acc), local);
                 rho0[v.offT + (int64_t)(i + 2) * v.ldp + k + 4] = (float)(acc * inv);

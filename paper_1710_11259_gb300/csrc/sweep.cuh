@@ -7,6 +7,12 @@
 // with L(Y) = A~ Y (along columns) and R(Y) = Y A~ (along rows); D after J
 // iterations is the ADI iterate Y_J of the paper's form started from Y_0 = 0 with
 // right-hand side rho_0 (the two forms agree term by term in exact arithmetic).
+// On a rectangle the equation is kx A~ Y + ky Y A~ = F~ with shifts p_j (row side)
+// and q_j (column side) of App. A's general intervals; the same steps then read
+//     c_j = (L - q_j/kx)^{-1} (R + p_j/ky)^{-1} rho_j,
+//     D  <- D - (q_j - p_j)/(kx ky) c_j,    rho_{j+1} = (L - p_j/kx)(R + q_j/ky) c_j,
+// (the scalars kx, ky of the solves and the stencils cancel), so the kernels only
+// see two solve shifts, two stencil shifts and one correction factor per iteration.
 //
 // Each banded solve is split into the two tridiagonals of App. B (even and odd
 // indices) and every tridiagonal into segments of S positions.  A pass solves its
@@ -67,8 +73,10 @@ struct SwProb {
     int n, S, P, N, ldp, J;
     int64_t off, rhs;      // element offset of rhs 0 / stride between right-hand sides (T arrays)
     int64_t soff, srhs;    // the same for the segment arrays ([P][2][N + 8] entries)
-    const Fac<T> *fac;     // [J][N + 4]
-    const T *q;            // [J] shifts
+    const Fac<T> *facR;    // [J][N + 4] tables of the row solves (shift -p_j / ky)
+    const Fac<T> *facC;    // [J][N + 4] tables of the column solves (shift q_j / kx); == facR on a square
+    const T *sh;           // [J][3]: {column-stencil shift -p_j/kx, row-stencil shift q_j/ky,
+                           //          correction factor -(q_j - p_j)/(kx ky)}; square: {q, q, -2q}
     const T *d, *e;        // bands of A~ at index i + 2, zero outside [0, n)
 };
 
@@ -96,6 +104,7 @@ struct TileProb {
     int64_t off, rhs;       // padded T arrays (as SwProb)
     const double *d, *e, *s;  // FP64 bands of A~ (d, e zero-padded to length n) and 1/sqrt(E)
     int pair0;              // index of (problem, rhs 0) among all pairs
+    double kx, ky;          // scales of the two second derivatives (1, 1 on [-1,1]^2)
 };
 
 struct TileArgs {

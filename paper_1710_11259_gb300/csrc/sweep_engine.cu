@@ -183,7 +183,7 @@ int SweepEngine<T>::autotune(const std::vector<int64_t> &ns, int nrhs, double to
     for (int S : cand) {
         SweepEngine<T> t;
         std::string e2;
-        int st = t.create(ns, nrhs, tol, tight, cap_, e2, S);
+        int st = t.create(ns, nrhs, tol, tight, cap_, e2, S, kx_, ky_);
         float ms = 0.f;
         if (st == FPS_OK) st = t.time_level(t.levels_.size() - 1, 2, ms, e2);
         t.release();
@@ -206,8 +206,10 @@ int SweepEngine<T>::autotune(const std::vector<int64_t> &ns, int nrhs, double to
 
 template <typename T>
 int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight,
-                           cudaStream_t setup_stream, std::string &err, int seg)
+                           cudaStream_t setup_stream, std::string &err, int seg, double kx, double ky)
 {
+    kx_ = kx;
+    ky_ = ky;
     constexpr bool kFP64 = sizeof(T) == 8;
     ns_ = ns;
     nrhs_ = nrhs;
@@ -327,6 +329,8 @@ int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol,
             t.e = bands64_ + o64 + n;
             t.s = bands64_ + o64 + 2 * n;
             t.pair0 = p * nrhs;
+            t.kx = kx_;
+            t.ky = ky_;
             o64 += 3 * n;
             oT += 2 * (N + 4);
             const int nt = (int)((n + 31) / 32);
@@ -388,32 +392,48 @@ int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol,
         Level L;
         L.tol = tols[li];
         L.J.resize(np);
+        // intervals of kx A~ (row side) and -ky A~ (column side): [a, b] = -kx [hi, lo],
+        // [c, d] = ky [lo, hi]; on a square (kx = ky) the symmetric route gives p = -q
+        const bool sym = kx_ == ky_;
+        const int ntab = sym ? 1 : 2;  // one table serves rows and columns on a square
         int64_t nfac = 0, nq = 0;
         for (int p = 0; p < np; ++p) {
-            L.J[p] = adi_iterations(-hi[p], -lo[p], lo[p], hi[p], L.tol);
+            L.J[p] = adi_iterations(-kx_ * hi[p], -kx_ * lo[p], ky_ * lo[p], ky_ * hi[p], L.tol);
             L.Jmax = std::max(L.Jmax, L.J[p]);
-            nfac += (int64_t)L.J[p] * (N_[p] + 4);
+            nfac += (int64_t)ntab * L.J[p] * (N_[p] + 4);
             nq += L.J[p];
         }
         ENG_CK(dalloc(&L.fac, (size_t)nfac));
-        ENG_CK(dalloc(&L.q, (size_t)nq));
+        ENG_CK(dalloc(&L.sh, (size_t)(3 * nq)));
         ENG_CK(dalloc(&L.d_probs, (size_t)np));
         ENG_CK(cudaMemsetAsync(L.fac, 0, sizeof(Fac<T>) * (size_t)nfac, cap_));
         FacJob<T> *d_jobs = nullptr;
-        ENG_CK(cudaMalloc((void **)&d_jobs, sizeof(FacJob<T>) * (size_t)nq));
+        ENG_CK(cudaMalloc((void **)&d_jobs, sizeof(FacJob<T>) * (size_t)(ntab * nq)));
         std::vector<SwProb<T>> probs(np);
         std::vector<FacJob<T>> jobs;
-        std::vector<T> qh;
-        jobs.reserve(nq);
-        qh.reserve(nq);
+        std::vector<T> shh;
+        jobs.reserve(ntab * nq);
+        shh.reserve(3 * nq);
         int64_t of = 0, oq = 0;
-        std::vector<double> q;
+        std::vector<double> q, pp;
         for (int p = 0; p < np; ++p) {
             const int64_t n = ns[p];
             const int N = N_[p];
-            zolotarev_shifts_symmetric(lo[p], hi[p], L.J[p], q);
+            const double a = -kx_ * hi[p], b = -kx_ * lo[p], c = ky_ * lo[p], d = ky_ * hi[p];
+            if (sym) {
+                zolotarev_shifts_symmetric(lo[p], hi[p], L.J[p], q);
+                pp.resize(q.size());
+                for (size_t u = 0; u < q.size(); ++u) {
+                    q[u] *= kx_;
+                    pp[u] = -q[u];
+                }
+            } else {
+                zolotarev_shifts(a, b, c, d, L.J[p], pp, q);
+            }
             inject_shift_fault(q);
-            if (!shifts_valid(q, lo[p], hi[p])) {
+            std::vector<double> mp(pp.size());
+            for (size_t u = 0; u < pp.size(); ++u) mp[u] = -pp[u];
+            if (!shifts_valid(q, c, d) || !shifts_valid(mp, -b, -a)) {
                 cudaFree(d_jobs);
                 levels_.push_back(std::move(L));
                 err = "shift list failed validation (a shift is not finite or lies outside the spectral interval)";
@@ -431,30 +451,36 @@ int SweepEngine<T>::create(const std::vector<int64_t> &ns, int nrhs, double tol,
             sp.rhs = (int64_t)(N + 4) * (N + 8);
             sp.soff = offS_[p];
             sp.srhs = (int64_t)P_[p] * 2 * (N + 8);
-            sp.fac = L.fac + of;
-            sp.q = L.q + oq;
+            sp.facR = L.fac + of;
+            sp.facC = L.fac + of + (sym ? 0 : (int64_t)L.J[p] * (N + 4));
+            sp.sh = L.sh + 3 * oq;
             sp.d = bandsT_ + obT[p];
             sp.e = bandsT_ + obT[p] + (N + 4);
+            for (int t = 0; t < ntab; ++t)
+                for (int j = 0; j < L.J[p]; ++j) {
+                    FacJob<T> jb;
+                    jb.q = t == 0 ? -pp[j] / ky_ : q[j] / kx_;  // row solve, then column solve
+                    jb.n = (int)n;
+                    jb.N = N;
+                    jb.S = S;
+                    jb.d = bands64_ + ob64[p];
+                    jb.e = bands64_ + ob64[p] + n;
+                    jb.out = L.fac + of + ((int64_t)t * L.J[p] + j) * (N + 4);
+                    jobs.push_back(jb);
+                }
             for (int j = 0; j < L.J[p]; ++j) {
-                FacJob<T> jb;
-                jb.q = q[j];
-                jb.n = (int)n;
-                jb.N = N;
-                jb.S = S;
-                jb.d = bands64_ + ob64[p];
-                jb.e = bands64_ + ob64[p] + n;
-                jb.out = L.fac + of + (int64_t)j * (N + 4);
-                jobs.push_back(jb);
-                qh.push_back((T)q[j]);
+                shh.push_back((T)(-pp[j] / kx_));                    // column-stencil shift
+                shh.push_back((T)(q[j] / ky_));                      // row-stencil shift
+                shh.push_back((T)(-(q[j] - pp[j]) / (kx_ * ky_)));  // correction factor
             }
-            of += (int64_t)L.J[p] * (N + 4);
+            of += (int64_t)ntab * L.J[p] * (N + 4);
             oq += L.J[p];
         }
         cudaError_t e1 = cudaMemcpyAsync(L.d_probs, probs.data(), sizeof(SwProb<T>) * np, cudaMemcpyHostToDevice, cap_);
         if (e1 == cudaSuccess)
             e1 = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(FacJob<T>) * jobs.size(), cudaMemcpyHostToDevice, cap_);
         if (e1 == cudaSuccess)
-            e1 = cudaMemcpyAsync(L.q, qh.data(), sizeof(T) * qh.size(), cudaMemcpyHostToDevice, cap_);
+            e1 = cudaMemcpyAsync(L.sh, shh.data(), sizeof(T) * shh.size(), cudaMemcpyHostToDevice, cap_);
         if (e1 == cudaSuccess) e1 = launch_fac_tables<T>(d_jobs, (int)jobs.size(), cap_);
         // the host vectors and the job table must outlive the asynchronous work
         if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(cap_);

@@ -22,8 +22,10 @@ public:
     // of A~ instead of Lemma B.2's.  `seg`: segment length of the partitioned sweeps
     // (64 or 128 for FP32, 64 for FP64); seg <= 0 lets the autotuner pick it (FP32).
     // Returns an fps_status; on error `err` holds a message.
+    // kx, ky: scales of the second derivatives along x and y (a kx^{-1/2} x ky^{-1/2}
+    // rectangle of half-widths; 1, 1 on [-1,1]^2).
     int create(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight, cudaStream_t setup_stream,
-               std::string &err, int seg = 0);
+               std::string &err, int seg = 0, double kx = 1.0, double ky = 1.0);
     void release();
 
     // Solve for device pointers F, X (packed as above) on stream st.  FP32: returns
@@ -55,8 +57,8 @@ private:
         int Jmax = 0;
         std::vector<int> J;
         SwProb<T> *d_probs = nullptr;
-        Fac<T> *fac = nullptr;
-        T *q = nullptr;
+        Fac<T> *fac = nullptr;  // row tables then (rectangle) column tables
+        T *sh = nullptr;        // per iteration: stencil shifts and correction factor
         cudaGraphExec_t graph = nullptr;
         std::vector<cudaEvent_t> ev;  // 4 per iteration when instrumented
     };
@@ -70,6 +72,7 @@ private:
     std::vector<int64_t> ns_;
     int nrhs_ = 1;
     double tol_ = 0;
+    double kx_ = 1.0, ky_ = 1.0;
     cudaStream_t cap_ = nullptr;
     std::vector<int> N_, P_;
     std::vector<int64_t> off64_, offT_, offS_;
