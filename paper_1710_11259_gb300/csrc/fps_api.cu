@@ -244,13 +244,22 @@ int create_square(fps_plan **out, int64_t n, double tol, int precision, bool tig
     double lo = fps::square_eps(n), hi = 1.0;
     if (tight && precision == FPS_FP64) fps::square_tight_interval(n, lo, hi);
     p->J = fps::adi_iterations(-kx * hi, -kx * lo, ky * lo, ky * hi, tol);
+    std::vector<double> mp;  // -p_j
     if (square) {
         fps::zolotarev_shifts_symmetric(lo, hi, p->J, p->q);
         for (double &v : p->q) v *= kx;
+        mp = p->q;
     } else {
         std::vector<double> pp;
         fps::zolotarev_shifts(-kx * hi, -kx * lo, ky * lo, ky * hi, p->J, pp, p->q);
+        for (double v : pp) mp.push_back(-v);
     }
+    // validated before anything is launched (every path, including the one-launch small path)
+    fps::inject_shift_fault(p->q);
+    if (!fps::shifts_valid(p->q, ky * lo, ky * hi) || !fps::shifts_valid(mp, kx * lo, kx * hi))
+        return bail(fail(FPS_ERR_INVALID_ARG, std::string(what) +
+                                                  ": shift list failed validation (a shift is not finite or lies "
+                                                  "outside the spectral interval)"));
     if (n > 40000) return bail(fail(FPS_ERR_UNSUPPORTED, std::string(what) + ": squares support n <= 40000"));
     if (nrhs > 256) return bail(fail(FPS_ERR_UNSUPPORTED, std::string(what) + ": squares support nrhs <= 256"));
     PCK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));

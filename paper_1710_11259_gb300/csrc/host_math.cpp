@@ -15,6 +15,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <string>
 
 namespace fps {
 
@@ -202,6 +204,21 @@ void zolotarev_shifts_symmetric_into(double lo, double hi, int J, double *q)
     for (int j = 0; j < J; ++j)
         if (2 * j + 1 > J) q[j] = kp / q[J - 1 - j];
     for (int j = 0; j < J; ++j) q[j] = hi * q[j];
+}
+
+bool shifts_valid(const std::vector<double> &q, double lo, double hi)
+{
+    for (double v : q)
+        if (!std::isfinite(v) || v < lo * (1.0 - 1e-12) || v > hi * (1.0 + 1e-12)) return false;
+    return !q.empty();
+}
+
+void inject_shift_fault(std::vector<double> &q)
+{
+    const char *f = std::getenv("FPS_INJECT_SHIFT_FAULT");
+    if (!f || q.empty()) return;
+    if (std::string(f) == "nan") q[0] = std::nan("");
+    else if (std::string(f) == "neg") q[0] = -q[0];
 }
 
 }  // namespace fps

@@ -34,4 +34,12 @@ void zolotarev_shifts_symmetric(double lo, double hi, int J, std::vector<double>
 // form above calls it, so both give the same bits).
 void zolotarev_shifts_symmetric_into(double lo, double hi, int J, double *q);
 
+// Every shift must be finite and lie in its interval [lo, hi] (up to rounding): the
+// shifted matrices are only guaranteed non-singular there.
+bool shifts_valid(const std::vector<double> &q, double lo, double hi);
+
+// Host-side fault injection for the failure-path tests: with FPS_INJECT_SHIFT_FAULT=nan
+// or =neg in the environment the first shift of the list is corrupted.
+void inject_shift_fault(std::vector<double> &q);
+
 }  // namespace fps

@@ -43,24 +43,6 @@ double bits_to_double(unsigned long long b)
 const double kLevelTols[] = {1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2};
 constexpr int kTileW = 64;       // rows of a row-pass tile / columns of a column-pass tile
 constexpr int kChainLines = 64;
-// Every shift must be finite and lie in [lo, hi] (up to rounding): the factors of
-// A~ - qI are only guaranteed non-singular there (sigma(A~) in [-hi, -lo], q > 0).
-bool shifts_valid(const std::vector<double> &q, double lo, double hi)
-{
-    for (double v : q)
-        if (!std::isfinite(v) || v < lo * (1.0 - 1e-12) || v > hi * (1.0 + 1e-12)) return false;
-    return !q.empty();
-}
-
-// Host-side fault injection for the failure-path tests: FPS_INJECT_SHIFT_FAULT=nan
-// or =neg corrupts the first shift of every list before validation.
-void inject_shift_fault(std::vector<double> &q)
-{
-    const char *f = std::getenv("FPS_INJECT_SHIFT_FAULT");
-    if (!f || q.empty()) return;
-    if (std::string(f) == "nan") q[0] = std::nan("");
-    else if (std::string(f) == "neg") q[0] = -q[0];
-}
 }  // namespace
 
 template <typename T>
