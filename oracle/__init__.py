@@ -87,6 +87,8 @@ def _lib(variant: str = "double") -> ctypes.CDLL:
             lib.orc_set_num_threads.argtypes = [ctypes.c_int]
             lib.orc_legendre_to_ctilde.argtypes = [ctypes.c_long, c_dp, c_dp]
             lib.orc_solution_to_legendre.argtypes = [ctypes.c_long, c_dp, c_dp]
+            lib.orc_legendre_to_ctilde_adjoint.argtypes = [ctypes.c_long, c_dp, c_dp]
+            lib.orc_solution_to_legendre_adjoint.argtypes = [ctypes.c_long, c_dp, c_dp]
             lib.orc_real_bytes.restype = ctypes.c_int
             _LIBS[variant] = lib
         return _LIBS[variant]
@@ -264,3 +266,22 @@ def solution_to_legendre(X) -> np.ndarray:
     U = np.zeros((n + 2, n + 2))
     _lib().orc_solution_to_legendre(n, _ptr(X), _ptr(U))
     return U
+
+
+def legendre_to_ctilde_adjoint(Fbar) -> np.ndarray:
+    """Gbar = B^T Fbar B, the transpose of ``legendre_to_ctilde`` (n x n)."""
+    Fbar = _f64(Fbar)
+    n = Fbar.shape[0]
+    Gbar = np.zeros_like(Fbar)
+    _lib().orc_legendre_to_ctilde_adjoint(n, _ptr(Fbar), _ptr(Gbar))
+    return Gbar
+
+
+def solution_to_legendre_adjoint(Ubar) -> np.ndarray:
+    """Xbar (n x n) = M^T B^{-T} Ubar B^{-1} M, the transpose of ``solution_to_legendre``
+    (Ubar is (n+2) x (n+2))."""
+    Ubar = _f64(Ubar)
+    n = Ubar.shape[0] - 2
+    Xbar = np.zeros((n, n))
+    _lib().orc_solution_to_legendre_adjoint(n, _ptr(Ubar), _ptr(Xbar))
+    return Xbar

@@ -868,6 +868,69 @@ void orc_solution_to_legendre(long n, const double *X, double *U)
     free(W);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Transposes of the two Legendre maps, for gradients through them (the         */
+/* chain rule of a loss L(U) back to G): with F = B G B^T the gradient in G is  */
+/* B^T Fbar B; with U = B^{-1} (M X M^T) B^{-T} (M taken (n+2) x n) the         */
+/* gradient in X is M^T (B^{-T} Ubar B^{-1}) M.                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Gbar (n x n) = B^T Fbar B. */
+void orc_legendre_to_ctilde_adjoint(long n, const double *Fbar, double *Gbar)
+{
+    real *T = malloc(sizeof(real) * (size_t)(n * n));
+    for (long j = 0; j < n; ++j) /* T = Fbar B: column b takes B[b][b] and B[b-2][b] */
+        for (long b = 0; b < n; ++b) {
+            real v = B_diag(b) * (real)Fbar[j * n + b];
+            if (b >= 2) v += B_off2(b - 2) * (real)Fbar[j * n + b - 2];
+            T[j * n + b] = v;
+        }
+    for (long a = 0; a < n; ++a) /* Gbar = B^T T: row a takes B[a][a] and B[a-2][a] */
+        for (long b = 0; b < n; ++b) {
+            real v = B_diag(a) * T[a * n + b];
+            if (a >= 2) v += B_off2(a - 2) * T[(a - 2) * n + b];
+            Gbar[a * n + b] = (double)v;
+        }
+    free(T);
+}
+
+/* Xbar (n x n) = M^T (B^{-T} Ubar B^{-1}) M for Ubar ((n+2) x (n+2)). */
+void orc_solution_to_legendre_adjoint(long n, const double *Ubar, double *Xbar)
+{
+    long m = n + 2;
+    real *V = malloc(sizeof(real) * (size_t)(m * m));
+    real *W1 = calloc((size_t)(n * m), sizeof(real));
+    for (long t = 0; t < m * m; ++t) V[t] = (real)Ubar[t];
+    for (long j = 0; j < m; ++j) /* B^T V' = V, column by column from the top (lower triangular) */
+        for (long i = 0; i < m; ++i) {
+            real v = V[i * m + j];
+            if (i >= 2) v -= B_off2(i - 2) * V[(i - 2) * m + j];
+            V[i * m + j] = v / B_diag(i);
+        }
+    for (long i = 0; i < m; ++i) /* V'' B = V', row by row from the left */
+        for (long k = 0; k < m; ++k) {
+            real v = V[i * m + k];
+            if (k >= 2) v -= B_off2(k - 2) * V[i * m + k - 2];
+            V[i * m + k] = v / B_diag(k);
+        }
+    for (long a = 0; a < n; ++a) /* W1 = M^T V, n x (n+2) */
+        for (long j = 0; j < m; ++j) {
+            real v = 0;
+            for (long i = a - 2; i <= a + 2; i += 2)
+                if (i >= 0 && i < m) v += M_entry(i, a) * V[i * m + j];
+            W1[a * m + j] = v;
+        }
+    for (long a = 0; a < n; ++a) /* Xbar = W1 M, n x n */
+        for (long b = 0; b < n; ++b) {
+            real v = 0;
+            for (long j = b - 2; j <= b + 2; j += 2)
+                if (j >= 0 && j < m) v += W1[a * m + j] * M_entry(j, b);
+            Xbar[a * n + b] = (double)v;
+        }
+    free(V);
+    free(W1);
+}
+
 /* Threads OpenMP will use (reported beside the CPU-baseline timings). */
 int orc_num_threads(void)
 {
