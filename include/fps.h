@@ -240,6 +240,41 @@ int fps_legendre_to_ctilde(int64_t n, const double *G, double *F, void *stream);
 int fps_solution_to_legendre(int64_t n, const double *X, double *U, void *stream);
 
 /*
+ * fps_poisson_dirichlet_solve -- Poisson with nonhomogeneous Dirichlet data (Sec. 6.1)
+ * on the plan's square or rectangle, in Legendre coefficients of the mapped
+ * variables x, y in [-1, 1] (row index = degree in y, column index = degree in x):
+ *   G   [nrhs][n][n]        f = sum G[a][b] P_a(y) P_b(x)
+ *   bc  [nrhs][4][n+2]      the traces g_W = u(-1, y), g_E = u(1, y), g_S = u(x, -1),
+ *                           g_N = u(x, 1), each sum_k bc[side][k] P_k(t)
+ *   U   [nrhs][n+2][n+2]    u = sum U[i][j] P_i(y) P_j(x)  (output)
+ * Sec. 6.1's four steps: (1) u_bc = the transfinite (Coons) interpolant of the traces
+ * (each corner value the mean of the two traces meeting there, so u_bc takes every
+ * trace exactly when the traces agree at the corners); (2) its Laplacian
+ * kx u_bc,xx + ky u_bc,yy, exact in the n x n block for n >= 2; (3) the homogeneous
+ * solve of the plan (Table 3.1 steps 1-4: F = B (G - lap u_bc) B^T, the ADI, the
+ * output map); (4) U = that solution + u_bc.  The plan must be a single square
+ * (fps_plan_create, dim 2) or rectangle (fps_plan_create_rect) plan, any precision,
+ * its nrhs right-hand sides solved together.  Buffers: device memory of the plan's
+ * device, caller-owned, U not overlapping G or bc; asynchronous on the plan's stream.
+ * The plan allocates two n x n FP64 work arrays per right-hand side on the first
+ * call and keeps them.  Errors: INVALID_ARG (NULL, host memory, overlap, batched or
+ * cube plan), NOT_CONVERGED (FP32_REFINE plans: U then holds the last iterate's
+ * solution), CUDA.
+ */
+int fps_poisson_dirichlet_solve(fps_plan *plan, const double *G, const double *bc, double *U);
+
+/*
+ * fps_poisson_dirichlet_adjoint -- gradients of a loss L(U) through
+ * fps_poisson_dirichlet_solve: given dLdU [nrhs][n+2][n+2] it writes dLdG [nrhs][n][n]
+ * and dLdbc [nrhs][4][n+2], the transpose of the linear map (G, bc) -> U applied to
+ * dLdU: the transposed output map, the same ADI solve (the solve map is
+ * self-adjoint), the transposed input map, and for the traces the transposed lifting
+ * minus the transposed Laplacian of the lifting applied to dLdG.  Same plan, buffer
+ * and error rules as the solve; the three buffers must not overlap.
+ */
+int fps_poisson_dirichlet_adjoint(fps_plan *plan, const double *dLdU, double *dLdG, double *dLdbc);
+
+/*
  * fps_poisson_square_solve_noalloc -- the FP64 square solve of fps_poisson_square_solve
  * (same shifts, iteration count and kernels) for n <= 256, without allocating
  * anything.  The paper has no counterpart: this entry point exists for callers that

@@ -129,17 +129,23 @@ def poisson_dirichlet_adjoint(Ubar, width: float = 2.0, height: float = 2.0, tol
     """Gradients (dL/dG, dL/dbc) of a loss L(U) from dL/dU: the transpose of the linear
     map (G, bc) -> U of ``poisson_dirichlet``, composed step by step in reverse."""
     Ubar = np.asarray(Ubar, dtype=np.float64)
-    m = Ubar.shape[0]
-    n = m - 2
-    kx, ky = rect_scales(width, height)
     Xbar = solution_to_legendre_adjoint(Ubar)
     Fbar = _solve(Xbar, width, height, tol)          # the solve map is self-adjoint
     Gbar = legendre_to_ctilde_adjoint(Fbar)
-    # U also depends on bc through lift (directly) and through -lift_laplacian in G:
-    # lap = ky D2 Xbc + kx Xbc D2^T cut to n x n, so its transpose sends Gbar to
-    # ky D2^T Gp + kx Gp D2 with Gp = Gbar padded to m x m.
+    return Gbar, traces_adjoint(Ubar, Gbar, width, height)
+
+
+def traces_adjoint(Ubar, Gbar, width: float = 2.0, height: float = 2.0) -> np.ndarray:
+    """The gradient in the traces given dL/dU and dL/dG: U depends on bc through the
+    lift (directly) and through -lift_laplacian in the right-hand side;
+    lap = ky D2 Xbc + kx Xbc D2^T cut to n x n, whose transpose sends Gbar to
+    ky D2^T Gp + kx Gp D2 (Gp = Gbar padded to m x m)."""
+    Ubar = np.asarray(Ubar, dtype=np.float64)
+    m = Ubar.shape[0]
+    n = m - 2
+    kx, ky = rect_scales(width, height)
     D2 = _d2_matrix(m)
     Gp = np.zeros((m, m))
     Gp[:n, :n] = Gbar
     Xbc_bar = Ubar - (ky * D2.T @ Gp + kx * Gp @ D2)
-    return Gbar, _lift_matrix_T(Xbc_bar)
+    return _lift_matrix_T(Xbc_bar)

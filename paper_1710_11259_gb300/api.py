@@ -69,7 +69,7 @@ EXPORTED = [
     "fps_status_string", "fps_last_error", "fps_zolotarev_shifts", "fps_square_bands", "fps_build_arch",
     "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
     "fps_square_spectral_interval", "fps_legendre_to_ctilde", "fps_solution_to_legendre", "fps_plan_pass_times",
-    "fps_probe_fma_rate", "fps_plan_create_rect",
+    "fps_probe_fma_rate", "fps_plan_create_rect", "fps_poisson_dirichlet_solve", "fps_poisson_dirichlet_adjoint",
 ]
 
 
@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
         L.fps_square_spectral_interval.argtypes = [i64, ctypes.c_int, dp, dp]
         L.fps_legendre_to_ctilde.argtypes = [i64, vp, vp, vp]
         L.fps_solution_to_legendre.argtypes = [i64, vp, vp, vp]
+        L.fps_poisson_dirichlet_solve.argtypes = [vp, vp, vp, vp]
+        L.fps_poisson_dirichlet_adjoint.argtypes = [vp, vp, vp, vp]
         _lib = L
         return L
 
@@ -308,7 +310,11 @@ def legendre_to_ctilde(G, F=None, stream: Optional[int] = None):
     import torch
 
     n = int(G.shape[-1])
+    if tuple(G.shape) != (n, n):
+        raise FpsError(-1, f"G has shape {tuple(G.shape)}; expected a square matrix")
     F = torch.empty_like(G) if F is None else F
+    if tuple(F.shape) != (n, n):
+        raise FpsError(-1, f"F has shape {tuple(F.shape)}; expected {(n, n)}")
     s = _current_stream() if stream is None else int(stream)
     _check(lib().fps_legendre_to_ctilde(n, ctypes.c_void_p(_ptr(G)), ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(s)))
     return F
@@ -319,10 +325,59 @@ def solution_to_legendre(X, U=None, stream: Optional[int] = None):
     import torch
 
     n = int(X.shape[-1])
+    if tuple(X.shape) != (n, n):
+        raise FpsError(-1, f"X has shape {tuple(X.shape)}; expected a square matrix")
     U = torch.empty((n + 2, n + 2), dtype=X.dtype, device=X.device) if U is None else U
+    if tuple(U.shape) != (n + 2, n + 2):
+        raise FpsError(-1, f"U has shape {tuple(U.shape)}; expected {(n + 2, n + 2)}")
     s = _current_stream() if stream is None else int(stream)
     _check(lib().fps_solution_to_legendre(n, ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(U)), ctypes.c_void_p(s)))
     return U
+
+
+def _dirichlet_shapes(plan: Plan):
+    """Shapes of (G or dL/dG, bc or dL/dbc, U or dL/dU) for a square / rectangle plan."""
+    if plan.dim != 2 or plan.batch_ns is not None:
+        raise FpsError(-1, "nonhomogeneous Dirichlet solves need a single square or rectangle plan")
+    n, m = plan.n, plan.n + 2
+    lead = (plan.nrhs,) if plan.nrhs > 1 else ()
+    return lead + (n, n), lead + (4, m), lead + (m, m)
+
+
+def _need_shape(x, shape, name):
+    if tuple(x.shape) != tuple(shape):
+        raise FpsError(-1, f"{name} has shape {tuple(x.shape)}; the plan expects {tuple(shape)}")
+
+
+def poisson_dirichlet_solve(plan: Plan, G, bc, U=None):
+    """Legendre coefficients U ((n+2) x (n+2)) of the solution with Dirichlet traces bc
+    ([g_W, g_E, g_S, g_N], each n+2 Legendre coefficients) and right-hand side G (n x n
+    Legendre coefficients); CUDA float64 tensors, a leading nrhs axis when nrhs > 1."""
+    import torch
+
+    sg, sb, su = _dirichlet_shapes(plan)
+    _need_shape(G, sg, "G")
+    _need_shape(bc, sb, "bc")
+    U = torch.empty(su, dtype=G.dtype, device=G.device) if U is None else U
+    _need_shape(U, su, "U")
+    _check(lib().fps_poisson_dirichlet_solve(plan.handle, ctypes.c_void_p(_ptr(G)), ctypes.c_void_p(_ptr(bc)),
+                                             ctypes.c_void_p(_ptr(U))))
+    return U
+
+
+def poisson_dirichlet_adjoint(plan: Plan, dLdU, dLdG=None, dLdbc=None):
+    """(dL/dG, dL/dbc) from dL/dU through poisson_dirichlet_solve."""
+    import torch
+
+    sg, sb, su = _dirichlet_shapes(plan)
+    _need_shape(dLdU, su, "dLdU")
+    dLdG = torch.empty(sg, dtype=dLdU.dtype, device=dLdU.device) if dLdG is None else dLdG
+    dLdbc = torch.empty(sb, dtype=dLdU.dtype, device=dLdU.device) if dLdbc is None else dLdbc
+    _need_shape(dLdG, sg, "dLdG")
+    _need_shape(dLdbc, sb, "dLdbc")
+    _check(lib().fps_poisson_dirichlet_adjoint(plan.handle, ctypes.c_void_p(_ptr(dLdU)), ctypes.c_void_p(_ptr(dLdG)),
+                                               ctypes.c_void_p(_ptr(dLdbc))))
+    return dLdG, dLdbc
 
 
 def poisson_square_solve_noalloc(F, X, tol: float = 1e-13, stream: Optional[int] = None) -> int:

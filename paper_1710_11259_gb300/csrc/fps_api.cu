@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <initializer_list>
 #include <vector>
 
 #include "../../include/fps.h"
@@ -14,6 +15,7 @@
 #include "small.cuh"
 #include "cube.h"
 #include "legendre.cuh"
+#include "dirichlet.cuh"
 #include "trace.h"
 #include "status.h"
 
@@ -94,6 +96,9 @@ struct fps_plan {
     bool instrument = false;
     int64_t launches_last = 0;
     double kx = 1.0, ky = 1.0;  // scales of u_xx and u_yy (rectangle plans)
+    // nonhomogeneous Dirichlet solves: C~ right-hand side, C~ solution, trace second
+    // derivatives and coefficient sums (allocated by the first such call)
+    double *dir_F = nullptr, *dir_X = nullptr, *dir_d2 = nullptr, *dir_ts = nullptr;
 };
 
 namespace {
@@ -107,6 +112,8 @@ void release(fps_plan *p)
     if (p->sm_bands) cudaFree(p->sm_bands);
     if (p->sm_q) cudaFree(p->sm_q);
     if (p->sm_pcr) cudaFree(p->sm_pcr);
+    for (double *b : {p->dir_F, p->dir_X, p->dir_d2, p->dir_ts})
+        if (b) cudaFree(b);
     if (p->eng32) {
         p->eng32->release();
         delete p->eng32;
@@ -302,6 +309,38 @@ int create_square(fps_plan **out, int64_t n, double tol, int precision, bool tig
 
 }  // namespace
 
+namespace {
+
+// Arguments shared by the Dirichlet solve and its adjoint: a single (non-batched)
+// square or rectangle plan, device buffers, scratch allocated on first use.
+int dirichlet_check(fps_plan *p, std::initializer_list<const void *> ptrs, const char *what)
+{
+    if (!p) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": plan is NULL");
+    if (p->dim != 2 || !p->batch_ns.empty())
+        return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": needs a single square or rectangle plan");
+    for (const void *q : ptrs) {
+        if (!q) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": NULL buffer");
+        if (!is_device_pointer(q)) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": buffers must be device memory");
+    }
+    if (!p->dir_F) {
+        const size_t nn = (size_t)p->total_elems;
+        FPS_CK(cudaMalloc((void **)&p->dir_F, sizeof(double) * nn));
+        FPS_CK(cudaMalloc((void **)&p->dir_X, sizeof(double) * nn));
+        FPS_CK(cudaMalloc((void **)&p->dir_d2, sizeof(double) * 4 * (size_t)p->n * p->nrhs));
+        FPS_CK(cudaMalloc((void **)&p->dir_ts, sizeof(double) * 8 * (size_t)p->nrhs));
+        p->bytes += (int64_t)sizeof(double) * (2 * (int64_t)nn + (4 * p->n + 8) * p->nrhs);
+    }
+    return FPS_OK;
+}
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + nb && y < x + na;
+}
+
+}  // namespace
+
 extern "C" {
 
 int fps_plan_create(fps_plan **out, int64_t n, int dim, double tol, int precision, int nrhs, void *stream)
@@ -472,6 +511,61 @@ int fps_poisson_adjoint(fps_plan *plan, const double *dLdX, double *dLdF)
     // The solve map is self-adjoint (see fps.h): same ADI, same shifts.
     if (plan && plan->dim == 3) return fps_poisson_cube_solve(plan, dLdX, dLdF);
     return solve_square(plan, dLdX, dLdF, "fps_poisson_adjoint");
+}
+
+int fps_poisson_dirichlet_solve(fps_plan *plan, const double *G, const double *bc, double *U)
+{
+    const char *what = "fps_poisson_dirichlet_solve";
+    fps::TraceRange tr(what);
+    if (plan) {
+        const size_t n = (size_t)plan->n, m = n + 2, R = (size_t)plan->nrhs;
+        if (overlaps(U, 8 * R * m * m, G, 8 * R * n * n) || overlaps(U, 8 * R * m * m, bc, 8 * R * 4 * m))
+            return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": U overlaps G or bc");
+    }
+    int st = dirichlet_check(plan, {G, bc, U}, what);
+    if (st != FPS_OK) return st;
+    DeviceGuard g(plan->device);
+    const int64_t n = plan->n, m = n + 2;
+    cudaStream_t s = plan->stream;
+    FPS_CK(fps::launch_dirichlet_prep(bc, plan->dir_d2, plan->dir_ts, n, plan->nrhs, s));       // steps 1-2
+    for (int r = 0; r < plan->nrhs; ++r)
+        FPS_CK(fps::launch_legendre_to_ctilde(G + r * n * n, plan->dir_F + r * n * n, n, s));
+    FPS_CK(fps::launch_dirichlet_rhs(plan->dir_F, plan->dir_d2, n, plan->nrhs, plan->kx, plan->ky, s));  // step 3
+    st = solve_square(plan, plan->dir_F, plan->dir_X, what);
+    if (st != FPS_OK && st != FPS_ERR_NOT_CONVERGED) return st;
+    const std::string msg = st == FPS_OK ? std::string() : g_last_error;
+    for (int r = 0; r < plan->nrhs; ++r)
+        FPS_CK(fps::launch_solution_to_legendre(plan->dir_X + r * n * n, U + r * m * m, n, s));
+    FPS_CK(fps::launch_dirichlet_lift(U, bc, plan->dir_ts, n, plan->nrhs, s));                   // step 4
+    if (st != FPS_OK) return fail(st, msg);
+    return FPS_OK;
+}
+
+int fps_poisson_dirichlet_adjoint(fps_plan *plan, const double *dLdU, double *dLdG, double *dLdbc)
+{
+    const char *what = "fps_poisson_dirichlet_adjoint";
+    fps::TraceRange tr(what);
+    if (plan) {
+        const size_t n = (size_t)plan->n, m = n + 2, R = (size_t)plan->nrhs;
+        if (overlaps(dLdU, 8 * R * m * m, dLdG, 8 * R * n * n) || overlaps(dLdU, 8 * R * m * m, dLdbc, 8 * R * 4 * m) ||
+            overlaps(dLdG, 8 * R * n * n, dLdbc, 8 * R * 4 * m))
+            return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": dLdU, dLdG and dLdbc must not overlap");
+    }
+    int st = dirichlet_check(plan, {dLdU, dLdG, dLdbc}, what);
+    if (st != FPS_OK) return st;
+    DeviceGuard g(plan->device);
+    const int64_t n = plan->n, m = n + 2;
+    cudaStream_t s = plan->stream;
+    for (int r = 0; r < plan->nrhs; ++r)
+        FPS_CK(fps::launch_solution_to_legendre_adjoint(dLdU + r * m * m, plan->dir_X + r * n * n, n, s));
+    st = solve_square(plan, plan->dir_X, plan->dir_F, what);  // the solve map is self-adjoint
+    if (st != FPS_OK && st != FPS_ERR_NOT_CONVERGED) return st;
+    const std::string msg = st == FPS_OK ? std::string() : g_last_error;
+    for (int r = 0; r < plan->nrhs; ++r)
+        FPS_CK(fps::launch_legendre_to_ctilde_adjoint(plan->dir_F + r * n * n, dLdG + r * n * n, n, s));
+    FPS_CK(fps::launch_dirichlet_bc_adjoint(dLdU, dLdG, dLdbc, n, plan->nrhs, plan->kx, plan->ky, s));
+    if (st != FPS_OK) return fail(st, msg);
+    return FPS_OK;
 }
 
 int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)

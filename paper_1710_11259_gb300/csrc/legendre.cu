@@ -108,6 +108,71 @@ __global__ void __launch_bounds__(256) solution_to_legendre_kernel(const double 
     }
 }
 
+// Transpose of the input map, Gbar = B^T Fbar B:
+//   Gbar[a][b] = sum_{i in {a, a-2}} sum_{j in {b, b-2}} B[i][a] B[j][b] Fbar[i][j],
+// with B[a][a] and B[a-2][a] the two entries of column a.  One thread per element.
+__global__ void __launch_bounds__(256) legendre_to_ctilde_adjoint_kernel(const double *__restrict__ Fb,
+                                                                         double *__restrict__ Gb, int64_t n)
+{
+    __shared__ double rd[kTC], ro[kTC], cd[kTC], co[kTC];  // column a of B: {B[a][a], B[a-2][a]} (0 if a < 2)
+    const int64_t a0 = (int64_t)blockIdx.y * kTC, b0 = (int64_t)blockIdx.x * kTC;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    auto diag = [](int64_t j) { return 1.0 / ((2.0 * (double)j + 1.0) * snorm(j)); };
+    auto off = [](int64_t j) { return j < 2 ? 0.0 : -1.0 / ((2.0 * (double)(j - 2) + 5.0) * snorm(j - 2)); };
+    if (tid < kTC) {
+        rd[tid] = diag(a0 + tid);
+        ro[tid] = off(a0 + tid);
+    } else if (tid < 2 * kTC) {
+        cd[tid - kTC] = diag(b0 + tid - kTC);
+        co[tid - kTC] = off(b0 + tid - kTC);
+    }
+    __syncthreads();
+    const int64_t b = b0 + threadIdx.x;
+    if (b >= n) return;
+    const bool b2 = b >= 2;
+    for (int r = threadIdx.y; r < kTC; r += blockDim.y) {
+        const int64_t a = a0 + r;
+        if (a >= n) break;
+        const double *f0 = Fb + a * n + b;
+        double row0 = cd[threadIdx.x] * f0[0];
+        if (b2) row0 = fma(co[threadIdx.x], f0[-2], row0);
+        double v = rd[r] * row0;
+        if (a >= 2) {
+            const double *f2 = f0 - 2 * n;
+            double row2 = cd[threadIdx.x] * f2[0];
+            if (b2) row2 = fma(co[threadIdx.x], f2[-2], row2);
+            v = fma(ro[r], row2, v);
+        }
+        Gb[a * n + b] = v;
+    }
+}
+
+// Transpose of the output map, Xbar = L^T Ubar L with L[a][a] = c_a, L[a+2][a] = -c_a:
+//   Xbar[a][k] = c_a c_k (Ubar[a][k] - Ubar[a][k+2] - Ubar[a+2][k] + Ubar[a+2][k+2]).
+__global__ void __launch_bounds__(256) solution_to_legendre_adjoint_kernel(const double *__restrict__ Ub,
+                                                                           double *__restrict__ Xb, int64_t n)
+{
+    __shared__ double rc[kTC], cc[kTC];
+    const int64_t m = n + 2;
+    const int64_t a0 = (int64_t)blockIdx.y * kTC, k0 = (int64_t)blockIdx.x * kTC;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    auto cval = [](int64_t a) {
+        const double A = (double)a;
+        return snorm(a) * (A + 1.0) * (A + 2.0) / (2.0 * A + 3.0);
+    };
+    if (tid < kTC) rc[tid] = cval(a0 + tid);
+    else if (tid < 2 * kTC) cc[tid - kTC] = cval(k0 + tid - kTC);
+    __syncthreads();
+    const int64_t k = k0 + threadIdx.x;
+    if (k >= n) return;
+    for (int r = threadIdx.y; r < kTC; r += blockDim.y) {
+        const int64_t a = a0 + r;
+        if (a >= n) break;
+        const double *u0 = Ub + a * m + k, *u2 = u0 + 2 * m;
+        Xb[a * n + k] = rc[r] * cc[threadIdx.x] * ((u0[0] - u0[2]) - (u2[0] - u2[2]));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_legendre_to_ctilde(const double *G, double *F, int64_t n, cudaStream_t st)
@@ -122,6 +187,20 @@ cudaError_t launch_solution_to_legendre(const double *X, double *U, int64_t n, c
     const int64_t m = n + 2;
     const dim3 block(kTC, 8), grid((unsigned)((m + kTC - 1) / kTC), (unsigned)((m + kTR - 1) / kTR));
     solution_to_legendre_kernel<<<grid, block, 0, st>>>(X, U, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_legendre_to_ctilde_adjoint(const double *Fbar, double *Gbar, int64_t n, cudaStream_t st)
+{
+    const dim3 block(kTC, 8), grid((unsigned)((n + kTC - 1) / kTC), (unsigned)((n + kTC - 1) / kTC));
+    legendre_to_ctilde_adjoint_kernel<<<grid, block, 0, st>>>(Fbar, Gbar, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solution_to_legendre_adjoint(const double *Ubar, double *Xbar, int64_t n, cudaStream_t st)
+{
+    const dim3 block(kTC, 8), grid((unsigned)((n + kTC - 1) / kTC), (unsigned)((n + kTC - 1) / kTC));
+    solution_to_legendre_adjoint_kernel<<<grid, block, 0, st>>>(Ubar, Xbar, n);
     return cudaGetLastError();
 }
 

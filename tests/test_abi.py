@@ -180,3 +180,30 @@ def test_noalloc_binding_rejects_non_square(L):
         with pytest.raises(api.FpsError) as e:
             api.poisson_square_solve_noalloc(F, X)
         assert e.value.status == -1
+
+
+def test_dirichlet_argument_errors(L):
+    """The Dirichlet entry points reject a NULL plan before any CUDA call, and the
+    binding rejects buffers of the wrong shape and batched or cube plans."""
+    import ctypes
+
+    buf = (ctypes.c_double * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.fps_poisson_dirichlet_solve(None, p, p, p) == -1
+    assert L.fps_poisson_dirichlet_adjoint(None, p, p, p) == -1
+    plan = api.Plan(0, 8, 2, 1)
+    G, bc, U = np.zeros((8, 8)), np.zeros((4, 10)), np.zeros((10, 10))
+    for args in [(np.zeros((8, 9)), bc, U), (G, np.zeros((4, 9)), U), (G, bc, np.zeros((8, 8))),
+                 (G, np.zeros((3, 10)), U)]:
+        with pytest.raises(api.FpsError) as e:
+            api.poisson_dirichlet_solve(plan, *args)
+        assert e.value.status == -1 and "shape" in str(e.value)
+    with pytest.raises(api.FpsError):
+        api.poisson_dirichlet_adjoint(plan, np.zeros((8, 8)), G, bc)
+    two = api.Plan(0, 8, 2, 2)
+    with pytest.raises(api.FpsError):
+        api.poisson_dirichlet_solve(two, G, bc, U)              # nrhs = 2 needs a leading axis
+    for other in [api.Plan(0, 8, 3, 1), api.Plan(0, 8, 2, 1, batch_ns=np.array([8, 4]))]:
+        with pytest.raises(api.FpsError) as e:
+            api.poisson_dirichlet_solve(other, G, bc, U)
+        assert "single square or rectangle" in str(e.value)

@@ -7,72 +7,19 @@ checked with the forward maps, including an exhaustive Jacobian at n = 3."""
 import numpy as np
 import pytest
 from numpy.polynomial import legendre as npleg
-from numpy.polynomial import polynomial as nppoly
 
 import oracle
 from oracle import dirichlet as odir
+from dirichlet_helpers import laplacian_by_quadrature, laplacian_power_route, traces
 
 RECTS = [(2.0, 2.0), (3.0, 0.75), (0.5, 4.0)]
-
-
-def _traces(U):
-    """Traces [g_W, g_E, g_S, g_N] of u = sum U[i, j] P_i(y) P_j(x) (P_k(+-1) = (+-1)^k)."""
-    m = U.shape[0]
-    alt = (-1.0) ** np.arange(m)
-    one = np.ones(m)
-    return np.stack([U @ alt, U @ one, alt @ U, one @ U])
-
-
-def _fixed(fn, v):
-    out = np.zeros(len(v))
-    r = fn(v)
-    out[: len(r)] = r
-    return out
-
-
-def _along_both(fn, C):
-    C = np.apply_along_axis(lambda v: _fixed(fn, v), 0, C)
-    return np.apply_along_axis(lambda v: _fixed(fn, v), 1, C)
-
-
-def _laplacian_power_route(U, kx, ky):
-    """Legendre coefficients of kx u_xx + ky u_yy computed through the power basis
-    (leg2poly, polyder, poly2leg): an independent route to the derivative."""
-    P = _along_both(npleg.leg2poly, U)
-    m = U.shape[0]
-    Pyy = np.zeros_like(P)
-    Pxx = np.zeros_like(P)
-    d = nppoly.polyder(P, 2, axis=0)
-    Pyy[: d.shape[0], :] = d
-    d = nppoly.polyder(P, 2, axis=1)
-    Pxx[:, : d.shape[1]] = d
-    return _along_both(npleg.poly2leg, ky * Pyy + kx * Pxx)
-
-
-def _laplacian_by_quadrature(U, kx, ky):
-    """Legendre coefficients of kx u_xx + ky u_yy by Gauss-Legendre projection of its
-    values, with P_j'' at the (interior) nodes from the Legendre equation,
-    (1-x^2) P'' = 2x P' - j(j+1) P and (1-x^2) P' = j (P_{j-1} - x P_j): a route that
-    uses no differentiation of coefficient series and stays accurate at high degree."""
-    m = U.shape[0]
-    x, w = npleg.leggauss(m + 4)
-    V = npleg.legvander(x, m)                       # P_0 .. P_m at the nodes
-    j = np.arange(m)
-    s = (1 - x * x)[:, None]
-    Pm1 = np.hstack([np.zeros((len(x), 1)), V[:, : m - 1]])
-    dV = j * (Pm1 - x[:, None] * V[:, :m]) / s
-    d2V = (2 * x[:, None] * dV - j * (j + 1) * V[:, :m]) / s
-    Vm = V[:, :m]
-    Fv = kx * Vm @ U @ d2V.T + ky * d2V @ U @ Vm.T  # values at (y_a, x_b)
-    Pw = Vm * w[:, None] * (2 * j + 1) / 2.0
-    return Pw.T @ Fv @ Pw
 
 
 def _random_compatible_bc(n, seed):
     rng = np.random.default_rng(seed)
     m = n + 2
     U = rng.standard_normal((m, m)) / np.add.outer(np.arange(m) + 1.0, np.arange(m) + 1.0) ** 2
-    return _traces(U)
+    return traces(U)
 
 
 @pytest.mark.parametrize("n", [1, 2, 5, 16])
@@ -104,10 +51,10 @@ def test_lift_laplacian_against_power_basis(w, h):
     kx, ky = oracle.rect_scales(w, h)
     bc = _random_compatible_bc(n, 5)
     L = odir.lift_laplacian(bc, kx, ky)
-    want = _laplacian_power_route(odir.lift(bc), kx, ky)
+    want = laplacian_power_route(odir.lift(bc), kx, ky)
     assert np.abs(want[n:, :]).max() < 1e-12 and np.abs(want[:, n:]).max() < 1e-12
     assert np.allclose(L, want[:n, :n], rtol=0, atol=1e-11 * np.abs(want).max())
-    want2 = _laplacian_by_quadrature(odir.lift(bc), kx, ky)
+    want2 = laplacian_by_quadrature(odir.lift(bc), kx, ky)
     assert np.allclose(L, want2[:n, :n], rtol=0, atol=1e-12 * np.abs(want2).max())
 
 
@@ -126,8 +73,8 @@ def _manufactured(n, seed):
 def test_manufactured_polynomial_solution(n, w, h):
     kx, ky = oracle.rect_scales(w, h)
     U = _manufactured(n, 11 + n)
-    G = _laplacian_by_quadrature(U, kx, ky)[:n, :n]
-    got = odir.poisson_dirichlet(G, _traces(U), w, h, 1e-14)
+    G = laplacian_by_quadrature(U, kx, ky)[:n, :n]
+    got = odir.poisson_dirichlet(G, traces(U), w, h, 1e-14)
     # f's coefficients grow like degree^2 (times the aspect ratio) against u's, so
     # rounding in f limits the recovered u to about that many ulps
     bar = 1e-14 * n * n * max(kx, ky) / min(kx, ky)
