@@ -155,7 +155,9 @@ int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X);
  * A~ Z A~ + c Z = R on every slice.  FPS_FP64: outer tolerance = the plan's tol,
  * middle and inner 1e-15, the paper's form of every level.  FPS_FP32_REFINE: the
  * nested ADI in FP32, every level in residual-propagating form, with level
- * tolerances (1e-3, 1e-6, 1e-7), inside an FP64 defect correction on the residual
+ * tolerances (1e-3, 1e-6, 1e-7) and every level's shifts on the Sturm-bisection
+ * interval of A~ (Lemma B.2's interval for FPS_FP64), inside an FP64 defect
+ * correction on the residual
  * R = G - (T_01 + T_02 + T_12) Y of the symmetrised equation (G = -F/sqrt(E_i E_j E_k))
  * until max |R| / max |G| <= tol (at most 12 rounds).  Plans: dim = 3, n <= 320.
  * X[(i*n + j)*n + k] pairs C~_i(x) C~_j(y) C~_k(z).  Host or device F and X.

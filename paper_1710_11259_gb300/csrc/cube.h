@@ -20,8 +20,10 @@ template <typename T>
 class CubeNested {
 public:
     // tol: outer tolerance of (2.9); tol_mid / tol_in: middle and inner levels;
-    // residual: run every level in residual-propagating form (the FP32 rounds).
-    int create(int64_t n, double tol, double tol_mid, double tol_in, bool residual, std::string &err);
+    // residual: run every level in residual-propagating form (the FP32 rounds);
+    // tight: every level's intervals from the Sturm-bisection interval of A~ instead
+    // of Lemma B.2's [-1, -1/(30 n^4)].
+    int create(int64_t n, double tol, double tol_mid, double tol_in, bool residual, bool tight, std::string &err);
     void release();
     // Y = the nested-ADI approximation of (T_01 + T_02 + T_12)^{-1} G (device tensors).
     int run(const T *G, T *Y, cudaStream_t st, std::string &err);
@@ -64,7 +66,8 @@ private:
     int add_stein(double c);
 
     int64_t n_ = 0;
-    double tol_ = 0, tol_mid_ = 0, tol_in_ = 0, eps_ = 0;
+    double tol_ = 0, tol_mid_ = 0, tol_in_ = 0;
+    double lo_ = 0, hi_ = 1;     // sigma(A~) in [-hi_, -lo_]
     bool residual_ = false;
     cudaStream_t st_ = nullptr;
     double *bd64_ = nullptr, *be64_ = nullptr;
