@@ -101,7 +101,9 @@ typedef struct {
  * A~ - q_j I once (Thomas pivots, App. B even/odd decoupling).
  * Every shift list is validated on the host before any kernel runs (finite, inside
  * the spectral interval).  Environment: FPS_MAX_REFINE_ROUNDS caps the refinement
- * rounds of FP32_REFINE plans (default 8); FPS_INJECT_SHIFT_FAULT=nan|neg corrupts
+ * rounds of FP32_REFINE plans (default 8 for squares, 12 for cubes);
+ * FPS_CUBE_STREAMING=1 makes FP32 cube plans run their inner level by whole-tensor
+ * line solves instead of the slice-resident cluster kernel; FPS_INJECT_SHIFT_FAULT=nan|neg corrupts
  * the first shift before validation (host-side fault injection for tests).
  * Errors: INVALID_ARG (n < 1, dim not 2/3, tol outside (0,1), nrhs < 1, out NULL, a
  * shift list that fails validation), CUDA (allocation or launch failure).  *out is
@@ -155,7 +157,9 @@ int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X);
  * A~ Z A~ + c Z = R on every slice.  FPS_FP64: outer tolerance = the plan's tol,
  * middle and inner 1e-15, the paper's form of every level.  FPS_FP32_REFINE: the
  * nested ADI in FP32, every level in residual-propagating form, with level
- * tolerances (1e-3, 1e-6, 1e-7) and every level's shifts on the Sturm-bisection
+ * tolerances (t, 1e-6, 1e-7), t in [1e-4, 1e-3] picked per plan for the fewest
+ * outer iterations over the predicted rounds (a round reduces the residual by about
+ * t/2), and every level's shifts on the Sturm-bisection
  * interval of A~ (Lemma B.2's interval for FPS_FP64), inside an FP64 defect
  * correction on the residual
  * R = G - (T_01 + T_02 + T_12) Y of the symmetrised equation (G = -F/sqrt(E_i E_j E_k))

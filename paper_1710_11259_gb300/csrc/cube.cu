@@ -29,12 +29,15 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/fps.h"
 #include "cube.h"
+#include "cube_slice.cuh"
 #include "device_info.h"
 #include "host_math.h"
 #include "trace.h"
@@ -564,6 +567,9 @@ int CubeNested<T>::create(int64_t n, double tol, double tol_mid, double tol_in, 
     CUBE_CK(cudaFuncSetAttribute(cube_line_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  line_smem_bytes<T>((int)n, false, 2)));
     fac_entry_ = -1;
+    slice_ = false;
+    if (std::is_same<T, float>::value && residual_ && std::getenv("FPS_CUBE_SLICE") != nullptr)
+        CUBE_CK(slice_setup((int)n, &slice_));
     return FPS_OK;
 }
 
@@ -711,6 +717,28 @@ int CubeNested<T>::stein_res(int ma, int mb, int entry, const T *R1, double r1, 
     int st = load_factors(entry, err);
     if (st != FPS_OK) return st;
     const Stein &S = steins_[entry];
+    if constexpr (std::is_same<T, float>::value) {
+        if (slice_) {  // all J iterations with every slice on chip (cube_slice.cu)
+            SliceArgs sa;
+            sa.fac = reinterpret_cast<const float2 *>(fac_);
+            sa.ab = ab_ + S.ab_off;
+            sa.J = S.J;
+            sa.R1 = R1;
+            sa.R2 = R2;
+            sa.r1 = (float)r1;
+            sa.r2 = (float)r2;
+            sa.Z = Z;
+            sa.accumulate = accumulate;
+            sa.d = bd_;
+            sa.e = be_;
+            sa.n = (int)n_;
+            sa.ma = ma;
+            sa.mb = mb;
+            CUBE_CK(launch_stein_slice(sa, st_));
+            ++launches;
+            return FPS_OK;
+        }
+    }
     T *rho = work_[0], *a1 = work_[1];
     CUBE_CK(solve(0, R1, r1, R2, r2, rho, mb, 1.0, 0.0, 0.0, false));                  // rho = R A~_b^{-1}
     for (int l = 0; l < S.J; ++l) {
@@ -815,11 +843,37 @@ template class CubeNested<float>;
 // CubeEngine
 // ===========================================================================
 
+// Outer tolerance t of the FP32 rounds.  A round reduces max|R| by about t/2
+// (measured 0.52 t at n = 256 with the middle and inner levels at 1e-6 and 1e-7), so
+// reaching `tol` takes R(t) = ceil(log(tol) / log(0.55 t)) rounds of J_outer(t) outer
+// iterations each; the candidate with the least R(t) J_outer(t) wins.  A round that
+// falls short only adds a round: the stopping test is the measured residual.
+double refinement_outer_tol(int64_t n, double tol)
+{
+    double lo = square_eps(n), hi = 1.0;
+    square_tight_interval(n, lo, hi);
+    const double e2 = lo * lo, h2 = hi * hi;
+    double best = CubeEngine::kRefTolOuter[0], best_cost = 1e300;
+    for (double t : CubeEngine::kRefTolOuter) {
+        const int R = std::max(1, (int)std::ceil(std::log(tol) / std::log(0.55 * t) - 1e-9));
+        const double cost = (double)R * adi_iterations(-h2, -e2, 2 * e2, 2 * h2, t);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = t;
+        }
+    }
+    return best;
+}
+
 int CubeEngine::create(int64_t n, double tol, int precision, std::string &err)
 {
     n_ = n;
     tol_ = tol;
     precision_ = precision;
+    if (const char *mr = std::getenv("FPS_MAX_REFINE_ROUNDS")) {  // cap on refinement rounds (>= 1)
+        const int v = std::atoi(mr);
+        if (v >= 1) max_rounds = v;
+    }
     std::vector<double> d, e, s;
     square_bands(n, d, e);
     inv_sqrt_E(n, s);
@@ -854,7 +908,8 @@ int CubeEngine::create(int64_t n, double tol, int precision, std::string &err)
         CUBE_CK(alloc((void **)&d_max_, sizeof(unsigned long long)));
         CUBE_CK(cudaMallocHost((void **)&h_max_, sizeof(unsigned long long)));
         n32_ = new CubeNested<float>();
-        st = n32_->create(n, kRefTol, kRefTolMid, kRefTolIn, true, true, err);
+        ref_tol_outer = refinement_outer_tol(n, tol);
+        st = n32_->create(n, ref_tol_outer, kRefTolMid, kRefTolIn, true, true, err);
         if (st != FPS_OK) return st;
         J_outer = J_outer_inner = n32_->J_outer;
         bytes += n32_->bytes;

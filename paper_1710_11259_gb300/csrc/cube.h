@@ -76,6 +76,7 @@ private:
     void *fac_ = nullptr;        // factor sets of the current Stein entry ({1/den, u} in T)
     double2 *ab_ = nullptr;      // (alpha, beta) of every factor set of every Stein entry
     int fac_entry_ = -1;         // entry whose factors fac_ holds (stream order makes reuse safe)
+    bool slice_ = false;         // FP32 inner solves by the slice-resident cluster kernel
     int max_sets_ = 0;
     std::vector<Stein> steins_;
     std::vector<Outer> outer_;
@@ -99,8 +100,11 @@ public:
     double resid_last = 0.0;     // max|G - T Y| / max|G| after the last solve (FP32 + refinement)
     int max_rounds = 12;
 
-    // Loose level tolerances of the FP32 rounds (outer, middle, inner).
-    static constexpr double kRefTol = 1e-3, kRefTolMid = 1e-6, kRefTolIn = 1e-7;
+    // Level tolerances of the FP32 rounds: middle and inner fixed; the outer one is
+    // picked per plan from kRefTolOuter (refinement_outer_tol).
+    static constexpr double kRefTolMid = 1e-6, kRefTolIn = 1e-7;
+    static constexpr double kRefTolOuter[] = {1e-3, 7e-4, 5e-4, 3e-4, 2e-4, 1e-4};
+    double ref_tol_outer = 1e-3;  // outer tolerance of the FP32 rounds in use
 
 private:
     int64_t n_ = 0;

@@ -216,3 +216,14 @@ def test_cube_adjoint_against_exact_solve_n17(api, precision, tol, bar):
     api.plan_destroy(plan)
     want = _cube_by_diagonalisation((X.detach() - Ustar).cpu().numpy())
     assert _relmax(g, want) <= bar
+
+
+@pytest.mark.parametrize("n", [5, 17, 48])
+def test_cube_refine_slice_resident_inner_level(api, monkeypatch, n):
+    """The opt-in slice-resident inner level (one 8-CTA cluster per slice, every inner
+    iteration on chip) against the exact solution by diagonalisation."""
+    monkeypatch.setenv("FPS_CUBE_SLICE", "1")
+    F = inputs.cube_rhs(n, 6)
+    X, info = _cube_plan_solve(api, F, "fp32_refine", 1e-10)
+    assert info["last_residual"] <= 1e-10
+    assert _relmax(X, _cube_by_diagonalisation(F)) <= 1e-10
