@@ -281,6 +281,48 @@ int fps_poisson_dirichlet_solve(fps_plan *plan, const double *G, const double *b
 int fps_poisson_dirichlet_adjoint(fps_plan *plan, const double *dLdU, double *dLdG, double *dLdbc);
 
 /*
+ * fps_plan_create_cylinder -- the Fourier modes k = kmin .. kmax (2 <= kmin) of
+ * Poisson's equation on the cylinder after the doubling-up of Sec. 4.1 (Case 1):
+ * for each mode, u_k(r, z) = r^2 (1 - r^2)(1 - z^2) w_k(r, z) with
+ * w_k = sum_{i,j < n} Y[i][j] C~_i(r) C~_j(z) solving
+ *     P Y M^T + Q Y D = F,   P = L1 - k^2 M,  Q = M_{r^2} M,
+ * L1 the matrix of r^2(1-r^2) d^2/dr^2 + (5-9r^2) r d/dr + 4(1-4r^2) (equal to
+ * M_{r^2} D + 5 M_r M D_1 + 14 M - 10 I), M of (3.7), D = diag(-(j+1)(j+2)); F the
+ * C~ x C~ coefficients of the mode's right-hand side f_k(r, z) (row index = degree in
+ * r).  The ADI of Algorithm 2 runs on A Y - Y B = P^{-1} F D^{-1}, A = P^{-1} Q,
+ * B = -M D^{-1}, multiplied through by P so that only banded solves and products
+ * remain; shifts (2.4) per mode from an interval of sigma(A_k) found by power
+ * iteration (widened by 3 %) and the tight interval of sigma(B); J of (2.9) per mode.
+ * FP64.  n in [4, 4096], nrhs right-hand sides per mode (e.g. the real and imaginary
+ * parts of f_k and f_{-k}).  Errors: INVALID_ARG, UNSUPPORTED (an interval or a pivot
+ * that cannot be formed), CUDA.
+ */
+int fps_plan_create_cylinder(fps_plan **out, int64_t n, int64_t kmin, int64_t kmax, double tol, int nrhs,
+                             void *stream);
+
+/*
+ * fps_poisson_cylinder_solve -- Y for every (mode, right-hand side) of a cylinder plan.
+ * F, Y: device pointers of the plan's device, [kmax - kmin + 1][nrhs][n][n] row-major,
+ * caller-owned, not overlapping; asynchronous on the plan's stream.  Errors:
+ * INVALID_ARG (not a cylinder plan, NULL, overlap, host memory), CUDA.
+ */
+int fps_poisson_cylinder_solve(fps_plan *plan, const double *F, double *Y);
+
+/*
+ * fps_cylinder_mode_interval -- host helper: the interval [*a, *b] (a < b < 0) the
+ * cylinder plan uses for sigma(A_k), A_k = P^{-1} Q of size n.  Errors: INVALID_ARG
+ * (n < 4, k < 2, NULL), UNSUPPORTED.
+ */
+int fps_cylinder_mode_interval(int64_t n, int64_t k, double *a, double *b);
+
+/*
+ * fps_cylinder_operators -- host helper: L1 and Q (n x n, row-major, caller-owned) of
+ * the cylinder modes, from the closed forms the plans use (k is not used: P = L1 -
+ * k^2 M).  Errors: INVALID_ARG.
+ */
+int fps_cylinder_operators(int64_t n, int64_t k, double *L1, double *Q);
+
+/*
  * fps_poisson_square_solve_noalloc -- the FP64 square solve of fps_poisson_square_solve
  * (same shifts, iteration count and kernels) for n <= 256, without allocating
  * anything.  The paper has no counterpart: this entry point exists for callers that

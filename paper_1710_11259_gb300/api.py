@@ -70,6 +70,7 @@ EXPORTED = [
     "fps_plan_set_instrument", "fps_plan_kernel_times", "fps_poisson_square_solve_noalloc",
     "fps_square_spectral_interval", "fps_legendre_to_ctilde", "fps_solution_to_legendre", "fps_plan_pass_times",
     "fps_probe_fma_rate", "fps_plan_create_rect", "fps_poisson_dirichlet_solve", "fps_poisson_dirichlet_adjoint",
+    "fps_plan_create_cylinder", "fps_poisson_cylinder_solve", "fps_cylinder_mode_interval", "fps_cylinder_operators",
 ]
 
 
@@ -113,6 +114,10 @@ def lib() -> ctypes.CDLL:
         L.fps_solution_to_legendre.argtypes = [i64, vp, vp, vp]
         L.fps_poisson_dirichlet_solve.argtypes = [vp, vp, vp, vp]
         L.fps_poisson_dirichlet_adjoint.argtypes = [vp, vp, vp, vp]
+        L.fps_plan_create_cylinder.argtypes = [ctypes.POINTER(vp), i64, i64, i64, ctypes.c_double, ctypes.c_int, vp]
+        L.fps_poisson_cylinder_solve.argtypes = [vp, vp, vp]
+        L.fps_cylinder_mode_interval.argtypes = [i64, i64, dp, dp]
+        L.fps_cylinder_operators.argtypes = [i64, i64, dp, dp]
         _lib = L
         return L
 
@@ -378,6 +383,50 @@ def poisson_dirichlet_adjoint(plan: Plan, dLdU, dLdG=None, dLdbc=None):
     _check(lib().fps_poisson_dirichlet_adjoint(plan.handle, ctypes.c_void_p(_ptr(dLdU)), ctypes.c_void_p(_ptr(dLdG)),
                                                ctypes.c_void_p(_ptr(dLdbc))))
     return dLdG, dLdbc
+
+
+class CylinderPlan(Plan):
+    """Plan over the cylinder's Fourier modes kmin .. kmax (Sec. 4.1, Case 1)."""
+
+    def __init__(self, handle: int, n: int, kmin: int, kmax: int, nrhs: int):
+        super().__init__(handle, n, 3, nrhs)
+        self.kmin, self.kmax = kmin, kmax
+
+    def shape(self):
+        return (self.kmax - self.kmin + 1, self.nrhs, self.n, self.n)
+
+
+def plan_create_cylinder(n: int, kmin: int, kmax: int, tol: float = 1e-13, nrhs: int = 1,
+                         stream: Optional[int] = None) -> CylinderPlan:
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else int(stream)
+    _check(lib().fps_plan_create_cylinder(ctypes.byref(h), int(n), int(kmin), int(kmax), float(tol), int(nrhs),
+                                          ctypes.c_void_p(s)))
+    return CylinderPlan(h.value, int(n), int(kmin), int(kmax), int(nrhs))
+
+
+def poisson_cylinder_solve(plan: CylinderPlan, F, Y=None):
+    """Y [modes][nrhs][n][n]: coefficients of w_k for every mode and right-hand side."""
+    if not isinstance(plan, CylinderPlan):
+        raise FpsError(-1, "not a cylinder plan")
+    Y = _out_like(F, Y)
+    _need_shape(F, plan.shape(), "F")
+    _need_shape(Y, plan.shape(), "Y")
+    _check(lib().fps_poisson_cylinder_solve(plan.handle, ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(_ptr(Y))))
+    return Y
+
+
+def cylinder_mode_interval(n: int, k: int):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fps_cylinder_mode_interval(int(n), int(k), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def cylinder_operators(n: int, k: int = 2):
+    L1 = np.zeros((n, n))
+    Q = np.zeros((n, n))
+    _check(lib().fps_cylinder_operators(int(n), int(k), _dp(L1), _dp(Q)))
+    return L1, Q
 
 
 def poisson_square_solve_noalloc(F, X, tol: float = 1e-13, stream: Optional[int] = None) -> int:

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libfps.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "sweep.cu", "sweep_engine.cu", "cube.cu", "legendre.cu", "fps_api.cu", "noalloc.cu", "probe.cu", "small.cu", "dirichlet.cu", "cube_slice.cu", "host_math.cpp"]
+SOURCES = ["kernels.cu", "sweep.cu", "sweep_engine.cu", "cube.cu", "legendre.cu", "fps_api.cu", "noalloc.cu", "probe.cu", "small.cu", "dirichlet.cu", "cube_slice.cu", "cylinder.cu", "host_math.cpp"]
 
 
 def _nvcc() -> str:

@@ -16,6 +16,7 @@
 #include "cube.h"
 #include "legendre.cuh"
 #include "dirichlet.cuh"
+#include "cylinder.h"
 #include "trace.h"
 #include "status.h"
 
@@ -99,6 +100,8 @@ struct fps_plan {
     // nonhomogeneous Dirichlet solves: C~ right-hand side, C~ solution, trace second
     // derivatives and coefficient sums (allocated by the first such call)
     double *dir_F = nullptr, *dir_X = nullptr, *dir_d2 = nullptr, *dir_ts = nullptr;
+    // cylinder Fourier modes |k| >= 2 (Sec. 4.1, Case 1)
+    fps::CylinderEngine *cyl = nullptr;
 };
 
 namespace {
@@ -125,6 +128,10 @@ void release(fps_plan *p)
     if (p->cube) {
         p->cube->release();
         delete p->cube;
+    }
+    if (p->cyl) {
+        p->cyl->release();
+        delete p->cyl;
     }
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
@@ -565,6 +572,93 @@ int fps_poisson_dirichlet_adjoint(fps_plan *plan, const double *dLdU, double *dL
         FPS_CK(fps::launch_legendre_to_ctilde_adjoint(plan->dir_F + r * n * n, dLdG + r * n * n, n, s));
     FPS_CK(fps::launch_dirichlet_bc_adjoint(dLdU, dLdG, dLdbc, n, plan->nrhs, plan->kx, plan->ky, s));
     if (st != FPS_OK) return fail(st, msg);
+    return FPS_OK;
+}
+
+int fps_plan_create_cylinder(fps_plan **out, int64_t n, int64_t kmin, int64_t kmax, double tol, int nrhs,
+                             void *stream)
+{
+    const char *what = "fps_plan_create_cylinder";
+    if (!out) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": out is NULL");
+    *out = nullptr;
+    if (n < 4) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": n must be >= 4");
+    if (n > 4096) return fail(FPS_ERR_UNSUPPORTED, std::string(what) + ": n must be <= 4096");
+    if (kmin < 2 || kmax < kmin) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": need 2 <= kmin <= kmax");
+    if (kmax - kmin + 1 > 65535 / std::max(nrhs, 1))
+        return fail(FPS_ERR_UNSUPPORTED, std::string(what) + ": too many (mode, right-hand side) pairs");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": tol must lie in (0, 1)");
+    if (nrhs < 1) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": nrhs must be >= 1");
+    fps::TraceRange tr(what);
+    fps_plan *p = new fps_plan();
+    p->n = n;
+    p->dim = 3;
+    p->tol = tol;
+    p->precision = FPS_FP64;
+    p->nrhs = nrhs;
+    p->stream = (cudaStream_t)stream;
+    p->total_elems = (kmax - kmin + 1) * nrhs * n * n;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return fail(FPS_ERR_CUDA, std::string(what) + ": no CUDA device");
+    }
+    p->cyl = new fps::CylinderEngine();
+    std::string err;
+    const int st = p->cyl->create(n, kmin, kmax, tol, nrhs, err);
+    if (st != FPS_OK) {
+        release(p);
+        return fail(st, std::string(what) + ": " + err);
+    }
+    p->J = p->cyl->Jmax;
+    p->bytes = p->cyl->bytes;
+    *out = p;
+    return FPS_OK;
+}
+
+int fps_poisson_cylinder_solve(fps_plan *plan, const double *F, double *Y)
+{
+    const char *what = "fps_poisson_cylinder_solve";
+    fps::TraceRange tr(what);
+    if (!plan || !plan->cyl) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": not a cylinder plan");
+    if (!F || !Y) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": NULL F or Y");
+    const size_t bytes = sizeof(double) * (size_t)plan->total_elems;
+    const char *f0 = (const char *)F, *y0 = (const char *)Y;
+    if (f0 < y0 + bytes && y0 < f0 + bytes) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and Y overlap");
+    if (!is_device_pointer(F) || !is_device_pointer(Y))
+        return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and Y must be device memory");
+    DeviceGuard g(plan->device);
+    std::string err;
+    const int st = plan->cyl->solve(F, Y, plan->stream, err);
+    plan->launches_last = plan->cyl->launches_last;
+    if (st != FPS_OK) return fail(st, std::string(what) + ": " + err);
+    return FPS_OK;
+}
+
+int fps_cylinder_mode_interval(int64_t n, int64_t k, double *a, double *b)
+{
+    if (n < 4 || k < 2 || !a || !b) return fail(FPS_ERR_INVALID_ARG, "fps_cylinder_mode_interval: need n >= 4, k >= 2");
+    if (fps::cyl_mode_interval(n, k, *a, *b) != FPS_OK)
+        return fail(FPS_ERR_UNSUPPORTED, "fps_cylinder_mode_interval: power iteration failed");
+    return FPS_OK;
+}
+
+int fps_cylinder_operators(int64_t n, int64_t k, double *L1, double *Q)
+{
+    if (n < 1 || n > 4096 || !L1 || !Q) return fail(FPS_ERR_INVALID_ARG, "fps_cylinder_operators: bad arguments");
+    (void)k;
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t i = 0; i < n; ++i) {
+            L1[a * n + i] = (std::llabs(a - i) == 2 || a == i) ? fps::cyl_L1(a, i) : 0.0;
+            double mm = 0.0;
+            auto Me = [](int64_t x, int64_t y) {
+                if (x < 0 || y < 0) return 0.0;
+                if (x == y) return fps::cyl_M_diag(x);
+                if (x == y + 2) return fps::cyl_M_off(y);
+                if (y == x + 2) return fps::cyl_M_off(x);
+                return 0.0;
+            };
+            for (int64_t c = a - 2; c <= a + 2; c += 2) mm += Me(a, c) * Me(c, i);
+            Q[a * n + i] = Me(a, i) - mm;
+        }
     return FPS_OK;
 }
 

@@ -1,0 +1,117 @@
+"""GPU parity of the cylinder Fourier modes |k| >= 2 (Sec. 4.1, Case 1) through the C
+ABI: against the oracle's Kronecker solve (small n) and its ADI at a tighter tolerance
+(n = 128), a manufactured solution whose right-hand side comes from the cylindrical
+Laplacian, and the independence of the modes in a batch.  A_k is only near-normal,
+so the ADI reaches tol within a factor of kappa_k (the condition number of A_k's
+eigenvectors): the bars are 10 x tol x kappa_k."""
+import numpy as np
+import pytest
+
+from oracle import cylinder as cyl
+from paper_1710_11259_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_11259_gb300 import api as _api
+    from paper_1710_11259_gb300 import build_ext
+
+    build_ext.build()
+    _api.lib()
+    return _api
+
+
+def _rhs(n, modes, nrhs, seed):
+    w = 1.0 / np.add.outer(np.arange(n) + 1.0, np.arange(n) + 1.0) ** 2
+    return np.ascontiguousarray(inputs.gaussian(seed, (modes, nrhs, n, n)) * w)
+
+
+def _kappa(n, k):
+    P, Q, M, D = cyl.mode_operators(n, k)
+    return float(np.linalg.cond(np.linalg.eig(np.linalg.solve(P, Q))[1]))
+
+
+def _solve(api, n, kmin, kmax, nrhs, F, tol=1e-13):
+    plan = api.plan_create_cylinder(n, kmin, kmax, tol, nrhs)
+    Y = api.poisson_cylinder_solve(plan, torch.from_numpy(F).cuda()).cpu().numpy()
+    info = api.plan_info(plan)
+    api.plan_destroy(plan)
+    return Y, info
+
+
+@pytest.mark.parametrize("n", [8, 16, 24])
+def test_cylinder_against_kronecker(api, n):
+    kmin, kmax, nrhs = 2, n // 2, 2
+    F = _rhs(n, kmax - kmin + 1, nrhs, 30 + n)
+    tol = 1e-13
+    Y, _ = _solve(api, n, kmin, kmax, nrhs, F, tol)
+    for m, k in enumerate(range(kmin, kmax + 1)):
+        bar = 10 * tol * _kappa(n, k)
+        for r in range(nrhs):
+            Ye = cyl.mode_solve_dense(F[m, r], k)
+            err = np.abs(Y[m, r] - Ye).max() / np.abs(Ye).max()
+            assert err <= bar, (k, r, err, bar)
+
+
+@pytest.mark.parametrize("k", [2, 5, 40])
+def test_cylinder_n128_against_oracle_adi(api, k):
+    n = 128
+    F = _rhs(n, 1, 1, 70 + k)
+    Y, info = _solve(api, n, k, k, 1, F, 1e-13)
+    Yo, _ = cyl.mode_adi(F[0, 0], k, 1e-15)
+    err = np.abs(Y[0, 0] - Yo).max() / np.abs(Yo).max()
+    assert err <= 10 * 1e-13 * _kappa(n, k), err
+
+
+def test_cylinder_manufactured(api):
+    """w(r, z) polynomial of parity k in r; F from the cylindrical Laplacian of
+    u = r^2(1-r^2)(1-z^2) w, projected by quadrature (as in the oracle's pin)."""
+    import sympy as sp
+    from scipy.special import roots_jacobi
+
+    from oracle import basis
+
+    r, z = sp.symbols("r z")
+    n = 24
+    rng = np.random.default_rng(3)
+    Fs, Ys, ks = [], [], [2, 3]
+    for k in ks:
+        w = sum(sp.Rational(int(rng.integers(-9, 10)), 5) * r ** a * z ** b
+                for a in range(k % 2, 9, 2) for b in range(9))
+        u = r ** 2 * (1 - r ** 2) * (1 - z ** 2) * w
+        f = sp.expand(sp.diff(u, r, 2) + sp.diff(u, r) / r - k ** 2 * u / r ** 2 + sp.diff(u, z, 2))
+        x, wq = roots_jacobi(n + 12, 1.0, 1.0)
+        Bm = basis.basis_matrix(n, x)
+        R, Z = np.meshgrid(x, x, indexing="ij")
+        proj = lambda expr: (Bm * wq) @ (sp.lambdify((r, z), expr, "numpy")(R, Z) + 0 * R) @ (Bm * wq).T
+        Fs.append(proj(f))
+        Ys.append(proj(w))
+    for k, F, Yt in zip(ks, Fs, Ys):
+        Y, _ = _solve(api, n, k, k, 1, np.ascontiguousarray(F[None, None]), 1e-14)
+        assert np.abs(Y[0, 0] - Yt).max() <= 1e-11 * _kappa(n, k) * np.abs(Yt).max()
+
+
+def test_cylinder_modes_independent_in_a_batch(api):
+    """Modes 2..32 solved together equal each mode solved alone (bit for bit)."""
+    n = 64
+    F = _rhs(n, 31, 2, 5)
+    Y, info = _solve(api, n, 2, 32, 2, F)
+    assert info["J"] >= 1
+    for k in (2, 17, 32):
+        Yk, _ = _solve(api, n, k, k, 2, np.ascontiguousarray(F[k - 2:k - 1]))
+        assert np.array_equal(Y[k - 2], Yk[0])
+
+
+def test_cylinder_rejects_host_buffers(api):
+    n = 16
+    plan = api.plan_create_cylinder(n, 2, 4, 1e-12, 1)
+    F = _rhs(n, 3, 1, 1)
+    with pytest.raises(api.FpsError) as e:
+        api.poisson_cylinder_solve(plan, F, np.empty_like(F))
+    api.plan_destroy(plan)
+    assert e.value.status == -1
