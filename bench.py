@@ -416,6 +416,41 @@ def dirichlet_line(api, inputs, stream, steps) -> dict:
             "refine_rounds": info["refine_rounds"], "steps": k}
 
 
+def cylinder_line(api, inputs, stream, steps, hbm) -> dict:
+    """Cylinder Fourier modes k = 2 .. 128 at n = 256 (Sec. 4.1, Case 1), four right-hand
+    sides per mode (the real and imaginary parts of f_k and f_-k), FP64 ADI to 1e-13:
+    127 x 4 systems of 256 x 256 unknowns in one plan."""
+    import numpy as np
+    import torch
+
+    n, kmin, kmax, nrhs = 256, 2, 128, 4
+    modes = kmax - kmin + 1
+    w = 1.0 / np.add.outer(np.arange(n) + 1.0, np.arange(n) + 1.0) ** 2
+    F = torch.empty((modes, nrhs, n, n), dtype=torch.float64, device="cuda")
+    for m in range(modes):
+        F[m].copy_(torch.from_numpy(inputs.gaussian(100 + m, (nrhs, n, n)) * w))
+    t0 = time.perf_counter()
+    plan = api.plan_create_cylinder(n, kmin, kmax, TOL_FP64, nrhs, stream=stream.cuda_stream)
+    plan_s = time.perf_counter() - t0
+    Y = api.poisson_cylinder_solve(plan, F)
+    k = max(1, min(steps, 3))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(k):
+        api.poisson_cylinder_solve(plan, F, Y)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / k
+    info = api.plan_info(plan)
+    api.plan_destroy(plan)
+    dofs = modes * nrhs * n * n
+    del F, Y
+    return {"workload": "cylinder modes k=2..128 (Sec. 4.1 Case 1), n=256, 4 right-hand sides per mode "
+                        "F = g/((1+i)(1+j))^2, FP64 ADI to 1e-13",
+            "value": dofs / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms, "dofs": dofs, "J_max": info["J"],
+            "kernel_launches": info["kernel_launches"], "plan_seconds": plan_s, "steps": k}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -618,6 +653,8 @@ def main() -> None:
         line["config4"] = config4(api, inputs, stream, args.steps)
         torch.cuda.empty_cache()
         line["dirichlet"] = dirichlet_line(api, inputs, stream, args.steps)
+        torch.cuda.empty_cache()
+        line["cylinder"] = cylinder_line(api, inputs, stream, args.steps, hbm)
         torch.cuda.empty_cache()
         if not args.no_cube:
             line["cube"] = cube_line(api, inputs, stream)

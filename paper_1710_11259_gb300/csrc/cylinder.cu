@@ -234,7 +234,8 @@ int cyl_mode_interval(int64_t n, int64_t k, double &a, double &b)
 // ---------------------------------------------------------------- device side
 namespace {
 
-constexpr int kCL = 32;  // lines per CTA
+constexpr int kCL = 32;        // lines per CTA
+constexpr int kCylThreads = 256;  // threads per CTA: all move the tile, the first 2 kCL sweep
 
 struct CylArgs {
     int n, modes, nrhs, kmin, Jmax, j;
@@ -252,145 +253,227 @@ enum { kMd = 0, kMe, kD, kL1d, kL1u, kL1l, kQ0, kQ2, kQ4, kBands };
 
 __host__ __device__ inline int pitch_of(int n) { return (n % 2 == 0) ? n + 1 : n; }
 
-// z kernel: blockIdx.x = block of 32 rows, blockIdx.y = (mode, rhs)
-__global__ void __launch_bounds__(2 * kCL) cyl_z_kernel(CylArgs A)
+constexpr int kC = 8;  // read-ahead chunk of the sweeps
+
+// z kernel: blockIdx.x = block of 32 rows, blockIdx.y = (mode, rhs).  Shared memory:
+// the tile [32][P], then the factor set of (M + p_j D) and the bands M_d, M_e, D.
+__global__ void __launch_bounds__(kCylThreads) cyl_z_kernel(CylArgs A)
 {
-    const int n = A.n, P = pitch_of(n);
+    const int n = A.n, P = pitch_of(n), st = n + 4;
     const int mode = blockIdx.y / A.nrhs;
     const int J = A.jcount[mode];
     if (A.j >= J) return;
     extern __shared__ double tile[];  // [kCL][P]
-    const double *band = A.bands;
+    double2 *fz = reinterpret_cast<double2 *>(tile + kCL * P);
+    double *md = reinterpret_cast<double *>(fz + n), *me = md + n, *dd = me + n;
     const int64_t pair = blockIdx.y;
     const int i0 = blockIdx.x * kCL, nl = min(kCL, n - i0);
     const double *Rin = A.first ? A.G : A.Rin;
     const double sgn = A.first ? -1.0 : 1.0;
     const int64_t base = pair * (int64_t)n * n + (int64_t)i0 * n;
-    for (int q = threadIdx.x; q < nl * n; q += blockDim.x) {
-        const int li = q / n, t = q - li * n;
-        tile[li * P + t] = sgn * Rin[base + (int64_t)li * n + t];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int li = warp; li < nl; li += kCylThreads / 32) {
+        const double *src = Rin + base + (int64_t)li * n;
+#pragma unroll 4
+        for (int t = lane; t < n; t += 32) tile[li * P + t] = sgn * src[t];
+    }
+    const double2 *fzg = A.zfac + (int64_t)(A.joff[mode] + A.j) * n;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        fz[t] = fzg[t];
+        md[t] = A.bands[kMd * st + t];
+        me[t] = A.bands[kMe * st + t];
+        dd[t] = A.bands[kD * st + t];
     }
     __syncthreads();
-    const double p = A.shifts[((int64_t)mode * A.Jmax + A.j) * 2 + 0];
     const double qq = A.shifts[((int64_t)mode * A.Jmax + A.j) * 2 + 1];
-    const double2 *fz = A.zfac + (int64_t)(A.joff[mode] + A.j) * n;
     const int li = threadIdx.x & (kCL - 1), par = threadIdx.x / kCL;
-    if (li < nl) {
+    if (threadIdx.x < 2 * kCL && li < nl) {
         double *row = tile + li * P;
         const int m = (n - par + 1) / 2;
         // W (M + p D) = -R1 D  (symmetric tridiagonal per parity)
-        double z = 0.0;
-        for (int s = 0; s < m; ++s) {
-            const int t = par + 2 * s;
-            const double in = -row[t] * band[kD * (n + 4) + t];
-            z = (s == 0) ? in : fma(-fz[t - 2].y, z, in);
-            row[t] = z;
+        double z = 0.0, up = 0.0;
+        for (int s0 = 0; s0 < m; s0 += kC) {
+            double in[kC], uf[kC];
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int t = par + 2 * min(s0 + u, m - 1);
+                in[u] = -row[t] * dd[t];
+                uf[u] = fz[t].y;
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (s0 + u < m) {
+                    z = fma(-up, z, in[u]);
+                    row[par + 2 * (s0 + u)] = z;
+                    up = uf[u];
+                }
         }
         double x = 0.0;
-        for (int s = m - 1; s >= 0; --s) {
-            const int t = par + 2 * s;
-            x = fma(-fz[t].y, x, fz[t].x * row[t]);
-            row[t] = x;
+        for (int s0 = m - 1; s0 >= 0; s0 -= kC) {
+            double zz[kC];
+            double2 ff[kC];
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int t = par + 2 * max(s0 - u, 0);
+                zz[u] = row[t];
+                ff[u] = fz[t];
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (s0 - u >= 0) {
+                    x = fma(-ff[u].y, x, ff[u].x * zz[u]);
+                    row[par + 2 * (s0 - u)] = x;
+                }
         }
         // -(W (M + q D)) D^{-1} along the row, in place with the previous W in a register
         double prev = 0.0;
-        for (int s = 0; s < m; ++s) {
-            const int t = par + 2 * s;
-            const double cur = row[t];
-            const double nxt = (t + 2 < n) ? row[t + 2] : 0.0;
-            double v = (band[kMd * (n + 4) + t] + qq * band[kD * (n + 4) + t]) * cur;
-            if (t >= 2) v = fma(band[kMe * (n + 4) + t - 2], prev, v);
-            if (t + 2 < n) v = fma(band[kMe * (n + 4) + t], nxt, v);
-            row[t] = -v / band[kD * (n + 4) + t];
-            prev = cur;
+        for (int s0 = 0; s0 < m; s0 += kC) {
+            double cur[kC + 1];
+#pragma unroll
+            for (int u = 0; u <= kC; ++u) {
+                const int t = par + 2 * (s0 + u);
+                cur[u] = t < n ? row[t] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (s0 + u < m) {
+                    const int t = par + 2 * (s0 + u);
+                    double v = fma(qq, dd[t], md[t]) * cur[u];
+                    if (t >= 2) v = fma(me[t - 2], prev, v);
+                    v = fma(me[t], cur[u + 1], v);  // me[t] = 0 when t + 2 >= n
+                    row[t] = -v / dd[t];
+                    prev = cur[u];
+                }
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < nl * n; q += blockDim.x) {
-        const int l = q / n, t = q - l * n;
-        const int64_t g = base + (int64_t)l * n + t;
-        A.Rout[g] = tile[l * P + t] + A.G[g];
+    for (int l = warp; l < nl; l += kCylThreads / 32) {
+        const int64_t g0 = base + (int64_t)l * n;
+#pragma unroll 4
+        for (int t = lane; t < n; t += 32) A.Rout[g0 + t] = tile[l * P + t] + A.G[g0 + t];
     }
 }
 
-// r kernel: blockIdx.x = block of 32 columns, blockIdx.y = (mode, rhs)
-__global__ void __launch_bounds__(2 * kCL) cyl_r_kernel(CylArgs A)
+// r kernel: blockIdx.x = block of 32 columns, blockIdx.y = (mode, rhs).  Shared memory:
+// the tile [n][32], the LU factors of (Q - q_j P) [n][6], and the bands of Q and of
+// P = L1 - k^2 M for this mode [6][n].
+__global__ void __launch_bounds__(kCylThreads) cyl_r_kernel(CylArgs A)
 {
-    const int n = A.n;
+    const int n = A.n, st = n + 4;
     const int mode = blockIdx.y / A.nrhs;
     const int J = A.jcount[mode];
     if (A.j >= J) return;
     const bool last = A.j + 1 == J;
     extern __shared__ double tile[];  // [n][kCL]
-    const double *band = A.bands;
+    double *fr = tile + (int64_t)n * kCL;   // [n][6]
+    double *q0 = fr + 6 * n, *q2 = q0 + n, *q4 = q2 + n, *pl = q4 + n, *pd = pl + n, *pu = pd + n;
     const int64_t pair = blockIdx.y;
     const int c0 = blockIdx.x * kCL, nc = min(kCL, n - c0);
     const int64_t base = pair * (int64_t)n * n + c0;
-    for (int q = threadIdx.x; q < n * kCL; q += blockDim.x) {
-        const int t = q / kCL, cj = q - t * kCL;
-        if (cj < nc) tile[t * kCL + cj] = A.Rin[base + (int64_t)t * n + cj];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < nc) {
+#pragma unroll 4
+        for (int t = warp; t < n; t += kCylThreads / 32) tile[t * kCL + lane] = A.Rin[base + (int64_t)t * n + lane];
+    }
+    const double *frg = A.rfac + (int64_t)(A.joff[mode] + A.j) * n * 6;
+    for (int q = threadIdx.x; q < 6 * n; q += blockDim.x) fr[q] = frg[q];
+    const double k2 = (double)(A.kmin + mode) * (double)(A.kmin + mode);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const double *bd = A.bands;
+        q0[t] = bd[kQ0 * st + t];
+        q2[t] = bd[kQ2 * st + t];
+        q4[t] = bd[kQ4 * st + t];
+        pd[t] = bd[kL1d * st + t] - k2 * bd[kMd * st + t];
+        pu[t] = bd[kL1u * st + t] - k2 * bd[kMe * st + t];
+        pl[t] = t >= 2 ? bd[kL1l * st + t] - k2 * bd[kMe * st + t - 2] : 0.0;
     }
     __syncthreads();
-    const double *fr = A.rfac + (int64_t)(A.joff[mode] + A.j) * n * 6;
     const int cj = threadIdx.x & (kCL - 1), par = threadIdx.x / kCL;
-    if (cj < nc) {
+    if (threadIdx.x < 2 * kCL && cj < nc) {
         double *col = tile + cj;
         const int m = (n - par + 1) / 2;
         // (Q - q P) X = R2: unit lower then upper sweep of the stored LU
         double y1 = 0.0, y2 = 0.0;  // y at s - 1, s - 2
-        for (int s = 0; s < m; ++s) {
-            const int t = par + 2 * s;
-            const double *f = fr + (int64_t)t * 6;
-            const double y = col[t * kCL] - f[0] * y1 - f[1] * y2;
-            col[t * kCL] = y;
-            y2 = y1;
-            y1 = y;
+        for (int s0 = 0; s0 < m; s0 += kC) {
+            double bb[kC], l1[kC], l2[kC];
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int t = par + 2 * min(s0 + u, m - 1);
+                bb[u] = col[t * kCL];
+                l1[u] = fr[t * 6 + 0];
+                l2[u] = fr[t * 6 + 1];
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (s0 + u < m) {
+                    const double y = fma(-l2[u], y2, fma(-l1[u], y1, bb[u]));
+                    col[(par + 2 * (s0 + u)) * kCL] = y;
+                    y2 = y1;
+                    y1 = y;
+                }
         }
         double x1 = 0.0, x2 = 0.0;  // x at s + 1, s + 2
-        for (int s = m - 1; s >= 0; --s) {
-            const int t = par + 2 * s;
-            const double *f = fr + (int64_t)t * 6;
-            const double x = (col[t * kCL] - f[3] * x1 - f[4] * x2) * f[2];
-            col[t * kCL] = x;
-            x2 = x1;
-            x1 = x;
+        for (int s0 = m - 1; s0 >= 0; s0 -= kC) {
+            double yy[kC], iu[kC], u1[kC], u2[kC];
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int t = par + 2 * max(s0 - u, 0);
+                yy[u] = col[t * kCL];
+                iu[u] = fr[t * 6 + 2];
+                u1[u] = fr[t * 6 + 3];
+                u2[u] = fr[t * 6 + 4];
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (s0 - u >= 0) {
+                    const double x = fma(-u2[u], x2, fma(-u1[u], x1, yy[u])) * iu[u];
+                    col[(par + 2 * (s0 - u)) * kCL] = x;
+                    x2 = x1;
+                    x1 = x;
+                }
         }
         if (!last) {  // (Q - p' P) X along the column, in place with two previous X in registers
             const double p = A.shifts[((int64_t)mode * A.Jmax + A.j + 1) * 2 + 0];
-            const double k2 = (double)(A.kmin + mode) * (double)(A.kmin + mode);
             double xm2 = 0.0, xm1 = 0.0;  // X at s - 2, s - 1
-            for (int s = 0; s < m; ++s) {
-                const int t = par + 2 * s;
-                const double x0 = col[t * kCL];
-                const double xp1 = (t + 2 < n) ? col[(t + 2) * kCL] : 0.0;
-                const double xp2 = (t + 4 < n) ? col[(t + 4) * kCL] : 0.0;
-                const double *b = band;
-                const int st = n + 4;
-                double qv = b[kQ0 * st + t] * x0;
-                if (t >= 2) qv = fma(b[kQ2 * st + t - 2], xm1, qv);
-                if (t >= 4) qv = fma(b[kQ4 * st + t - 4], xm2, qv);
-                if (t + 2 < n) qv = fma(b[kQ2 * st + t], xp1, qv);
-                if (t + 4 < n) qv = fma(b[kQ4 * st + t], xp2, qv);
-                const double pd = b[kL1d * st + t] - k2 * b[kMd * st + t];
-                double pv = pd * x0;
-                if (t >= 2) pv = fma(b[kL1l * st + t] - k2 * b[kMe * st + t - 2], xm1, pv);
-                if (t + 2 < n) pv = fma(b[kL1u * st + t] - k2 * b[kMe * st + t], xp1, pv);
-                col[t * kCL] = fma(-p, pv, qv);
-                xm2 = xm1;
-                xm1 = x0;
+            for (int s0 = 0; s0 < m; s0 += kC) {
+                double xv[kC + 2];
+#pragma unroll
+                for (int u = 0; u < kC + 2; ++u) {
+                    const int t = par + 2 * (s0 + u);
+                    xv[u] = t < n ? col[t * kCL] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kC; ++u)
+                    if (s0 + u < m) {
+                        const int t = par + 2 * (s0 + u);
+                        // q2[t], q4[t], pu[t] are zero past the end of the chain
+                        double qv = fma(q4[t], xv[u + 2], fma(q2[t], xv[u + 1], q0[t] * xv[u]));
+                        double pv = fma(pu[t], xv[u + 1], pd[t] * xv[u]);
+                        if (t >= 2) {
+                            qv = fma(q2[t - 2], xm1, qv);
+                            pv = fma(pl[t], xm1, pv);
+                        }
+                        if (t >= 4) qv = fma(q4[t - 4], xm2, qv);
+                        col[t * kCL] = fma(-p, pv, qv);
+                        xm2 = xm1;
+                        xm1 = xv[u];
+                    }
             }
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < n * kCL; q += blockDim.x) {
-        const int t = q / kCL, c = q - t * kCL;
-        if (c < nc) {
-            const int64_t g = base + (int64_t)t * n + c;
-            if (last) A.Y[g] = tile[t * kCL + c];
-            else A.Rout[g] = tile[t * kCL + c] - A.G[g];
+    if (lane < nc) {
+#pragma unroll 4
+        for (int t = warp; t < n; t += kCylThreads / 32) {
+            const int64_t g = base + (int64_t)t * n + lane;
+            if (last) A.Y[g] = tile[t * kCL + lane];
+            else A.Rout[g] = tile[t * kCL + lane] - A.G[g];
         }
     }
 }
+
+int z_smem(int n) { return (int)sizeof(double) * (kCL * pitch_of(n) + 2 * n + 3 * n); }
+int r_smem(int n) { return (int)sizeof(double) * (kCL * n + 6 * n + 6 * n); }
 
 // G = F D^{-1} (column j scaled by 1 / D_jj)
 __global__ void cyl_scale_kernel(const double *F, double *G, int n, int64_t total)
@@ -534,7 +617,7 @@ int CylinderEngine::create(int64_t n_, int64_t kmin_, int64_t kmax_, double tol,
     CYL_CK(cudaMemcpy(shifts_, sh.data(), sizeof(double) * sh.size(), cudaMemcpyHostToDevice));
     CYL_CK(cudaMemcpy(joff_, joff.data(), sizeof(int) * modes, cudaMemcpyHostToDevice));
     CYL_CK(cudaMemcpy(jcount_, jc.data(), sizeof(int) * modes, cudaMemcpyHostToDevice));
-    const int zs = (int)(sizeof(double) * kCL * pitch_of((int)n)), rs = (int)(sizeof(double) * kCL * n);
+    const int zs = z_smem((int)n), rs = r_smem((int)n);
     CYL_CK(cudaFuncSetAttribute(cyl_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, zs));
     CYL_CK(cudaFuncSetAttribute(cyl_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rs));
     return FPS_OK;
@@ -569,17 +652,17 @@ int CylinderEngine::solve(const double *F, double *Y, cudaStream_t st, std::stri
     A.G = G_;
     A.Y = Y;
     const dim3 grid((unsigned)((n + kCL - 1) / kCL), (unsigned)(modes * nrhs));
-    const int zs = (int)(sizeof(double) * kCL * pitch_of((int)n)), rs = (int)(sizeof(double) * kCL * n);
+    const int zs = z_smem((int)n), rs = r_smem((int)n);
     for (int j = 0; j < Jmax; ++j) {
         A.j = j;
         A.first = j == 0;
         A.Rin = R1_;
         A.Rout = R2_;
-        cyl_z_kernel<<<grid, 2 * kCL, zs, st>>>(A);
+        cyl_z_kernel<<<grid, kCylThreads, zs, st>>>(A);
         A.first = false;
         A.Rin = R2_;
         A.Rout = R1_;
-        cyl_r_kernel<<<grid, 2 * kCL, rs, st>>>(A);
+        cyl_r_kernel<<<grid, kCylThreads, rs, st>>>(A);
         launches_last += 2;
         CYL_CK(cudaGetLastError());
     }

@@ -3,7 +3,8 @@ ABI: against the oracle's Kronecker solve (small n) and its ADI at a tighter tol
 (n = 128), a manufactured solution whose right-hand side comes from the cylindrical
 Laplacian, and the independence of the modes in a batch.  A_k is only near-normal,
 so the ADI reaches tol within a factor of kappa_k (the condition number of A_k's
-eigenvectors): the bars are 10 x tol x kappa_k."""
+eigenvectors): the bars are 10 x tol x kappa_k, plus at n >= 64 the accuracy floor of
+the FP64 iteration (see below)."""
 import numpy as np
 import pytest
 
@@ -58,6 +59,22 @@ def test_cylinder_against_kronecker(api, n):
             assert err <= bar, (k, r, err, bar)
 
 
+# The paper's form of the ADI in FP64 does not get closer to the exact solution than
+# about 1e-12 at n = 64 and 1e-11 at n = 128, whatever the tolerance: the oracle's own
+# ADI at tol 1e-15 is 1.8e-12 from the Kronecker solution at n = 64, k = 32, and its
+# tol 1e-13 and 1e-15 results differ by 4.9e-12 at n = 128, k = 40 (P has entries up
+# to k^2 + n^2 and every step forms (Q - p P) X on the whole iterate).  The bars below
+# add that floor to 10 x tol x kappa_k.
+@pytest.mark.parametrize("k", [2, 16, 32])
+def test_cylinder_n64_against_kronecker(api, k):
+    n = 64
+    F = _rhs(n, 1, 1, 50 + k)
+    Y, _ = _solve(api, n, k, k, 1, F, 1e-13)
+    Ye = cyl.mode_solve_dense(F[0, 0], k)
+    err = np.abs(Y[0, 0] - Ye).max() / np.abs(Ye).max()
+    assert err <= 10 * 1e-13 * _kappa(n, k) + 1e-11, err
+
+
 @pytest.mark.parametrize("k", [2, 5, 40])
 def test_cylinder_n128_against_oracle_adi(api, k):
     n = 128
@@ -65,7 +82,7 @@ def test_cylinder_n128_against_oracle_adi(api, k):
     Y, info = _solve(api, n, k, k, 1, F, 1e-13)
     Yo, _ = cyl.mode_adi(F[0, 0], k, 1e-15)
     err = np.abs(Y[0, 0] - Yo).max() / np.abs(Yo).max()
-    assert err <= 10 * 1e-13 * _kappa(n, k), err
+    assert err <= 10 * 1e-13 * _kappa(n, k) + 3e-11, err
 
 
 def test_cylinder_manufactured(api):
