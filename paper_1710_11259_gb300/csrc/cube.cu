@@ -47,6 +47,7 @@ namespace fps {
 namespace {
 
 constexpr int kLines = 32;  // lines per CTA of the solve kernels
+constexpr int kLineThreads = 128;  // threads per CTA: all move the tiles, the first 2 kLines sweep
 constexpr int kU = 8;       // global loads in flight per thread in the solve output phase
 
 template <typename T>
@@ -168,7 +169,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 // 1): kLines lines adjacent in mode 2, one CTA per (index of the other strided mode,
 // block of kLines), tile [t][line].
 template <typename T, bool CONTIG>
-__global__ void __launch_bounds__(64) cube_line_kernel(const typename V2<T>::type *__restrict__ fac, const T *R1,
+__global__ void __launch_bounds__(kLineThreads) cube_line_kernel(const typename V2<T>::type *__restrict__ fac, const T *R1,
                                                        T s1, const T *R2, T s2, T *X, int n, int mode, T oscale,
                                                        T oin, T oacc, bool preband, const T *__restrict__ d,
                                                        const T *__restrict__ e)
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(64) cube_line_kernel(const typename V2<T>::typ
     T *Z = preband ? B : A;  // z, then x
     const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
     const int m = (n - par + 1) / 2;  // unknowns of this parity: t = par + 2 i, i < m
-    if (lane < nl) {
+    if (threadIdx.x < 2 * kLines && lane < nl) {
         // Both sweeps in chunks of kC steps: the chunk's operands are read from shared
         // memory first, so only the kC dependent FMAs remain on the critical path.
         constexpr int kC = 8;
@@ -620,12 +621,12 @@ cudaError_t CubeNested<T>::solve(int set, const T *R1, double s1, const T *R2, d
     if (mode == 2) {
         const int blocks = (n * n + kLines - 1) / kLines;
         const int smem = line_smem_bytes<T>(n, true, ntiles);
-        cube_line_kernel<T, true><<<blocks, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
+        cube_line_kernel<T, true><<<blocks, kLineThreads, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
                                                                      (T)oscale, (T)oin, (T)oacc, preband, bd_, be_);
     } else {
         const int nkb = (n + kLines - 1) / kLines;
         const int smem = line_smem_bytes<T>(n, false, ntiles);
-        cube_line_kernel<T, false><<<n * nkb, 2 * kLines, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
+        cube_line_kernel<T, false><<<n * nkb, kLineThreads, smem, st_>>>(fac, R1, (T)s1, R2, (T)s2, X, n, mode,
                                                                        (T)oscale, (T)oin, (T)oacc, preband, bd_,
                                                                        be_);
     }
