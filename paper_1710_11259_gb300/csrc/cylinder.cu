@@ -256,7 +256,7 @@ __host__ __device__ inline int pitch_of(int n) { return (n % 2 == 0) ? n + 1 : n
 constexpr int kC = 8;  // read-ahead chunk of the sweeps
 
 // z kernel: blockIdx.x = block of 32 rows, blockIdx.y = (mode, rhs).  Shared memory:
-// the tile [32][P], then the factor set of (M + p_j D) and the bands M_d, M_e, D.
+// the tile [32][P], then the factor set of (M + p_j D), the bands M_d, M_e, D and -1/D.
 __global__ void __launch_bounds__(kCylThreads) cyl_z_kernel(CylArgs A)
 {
     const int n = A.n, P = pitch_of(n), st = n + 4;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kCylThreads) cyl_z_kernel(CylArgs A)
     if (A.j >= J) return;
     extern __shared__ double tile[];  // [kCL][P]
     double2 *fz = reinterpret_cast<double2 *>(tile + kCL * P);
-    double *md = reinterpret_cast<double *>(fz + n), *me = md + n, *dd = me + n;
+    double *md = reinterpret_cast<double *>(fz + n), *me = md + n, *dd = me + n, *nid = dd + n;  // nid = -1/D
     const int64_t pair = blockIdx.y;
     const int i0 = blockIdx.x * kCL, nl = min(kCL, n - i0);
     const double *Rin = A.first ? A.G : A.Rin;
@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(kCylThreads) cyl_z_kernel(CylArgs A)
         md[t] = A.bands[kMd * st + t];
         me[t] = A.bands[kMe * st + t];
         dd[t] = A.bands[kD * st + t];
+        nid[t] = -1.0 / dd[t];
     }
     __syncthreads();
     const double qq = A.shifts[((int64_t)mode * A.Jmax + A.j) * 2 + 1];
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kCylThreads) cyl_z_kernel(CylArgs A)
                     double v = fma(qq, dd[t], md[t]) * cur[u];
                     if (t >= 2) v = fma(me[t - 2], prev, v);
                     v = fma(me[t], cur[u + 1], v);  // me[t] = 0 when t + 2 >= n
-                    row[t] = -v / dd[t];
+                    row[t] = v * nid[t];
                     prev = cur[u];
                 }
         }
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(kCylThreads) cyl_r_kernel(CylArgs A)
     }
 }
 
-int z_smem(int n) { return (int)sizeof(double) * (kCL * pitch_of(n) + 2 * n + 3 * n); }
+int z_smem(int n) { return (int)sizeof(double) * (kCL * pitch_of(n) + 2 * n + 4 * n); }
 int r_smem(int n) { return (int)sizeof(double) * (kCL * n + 6 * n + 6 * n); }
 
 // G = F D^{-1} (column j scaled by 1 / D_jj)
