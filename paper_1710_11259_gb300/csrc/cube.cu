@@ -365,6 +365,162 @@ __global__ void __launch_bounds__(kLineThreads) cube_line_kernel(const typename 
     }
 }
 
+// The two solves along `ma` of one residual-form inner iteration (stein_res) in one
+// launch, both with the set (A~ - q): with w = rho + (p - q) a1,
+//   rho <- (q - p) (A~ - q)^{-1} w + w,     Z <- (q - p) (A~ - q)^{-1} a1 + zacc Z.
+// Strided modes only (ma is 0 or 1); tiles [t][line]: A holds rho, then the z of the
+// w chain, then the new rho; B holds a1, then the z and x of the a1 chain.  The back
+// sweep recovers w_t = z_t + u_{t-2} z_{t-2} from the forward values below t (not yet
+// overwritten), so no third tile is needed.  Each thread runs both dependency chains.
+template <typename T>
+__global__ void __launch_bounds__(kLineThreads) cube_dual_kernel(const typename V2<T>::type *__restrict__ fac, T *rho,
+                                                                 const T *a1, T *Z, int n, int mode, T pq, T qp,
+                                                                 T zacc)
+{
+    using F2 = typename V2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F2 *fs = reinterpret_cast<F2 *>(smem_raw);
+    T *A = reinterpret_cast<T *>(fs + n);
+    T *B = A + kLines * n;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) fs[t] = fac[t];
+    const int nkb = (n + kLines - 1) / kLines;
+    const int other = blockIdx.x / nkb, k0 = (blockIdx.x % nkb) * kLines;
+    const int64_t nn = (int64_t)n * n;
+    const int nl = min(kLines, n - k0);
+    const int64_t gbase = ((mode == 0) ? (int64_t)other * n : (int64_t)other * nn) + k0;
+    const int64_t gt = (mode == 0) ? nn : (int64_t)n;
+    constexpr int V = 16 / (int)sizeof(T);
+    const bool vec = nl == kLines && ((gt * (int64_t)sizeof(T)) % 16 == 0) && ((gbase * (int64_t)sizeof(T)) % 16 == 0) &&
+                     (((uintptr_t)rho & 15) == 0) && (((uintptr_t)a1 & 15) == 0) && (((uintptr_t)Z & 15) == 0) &&
+                     ((n * (int)sizeof(F2)) % 16 == 0);
+    const int total = kLines * n;
+    if (vec) {
+        for (int q = threadIdx.x * V; q < total; q += blockDim.x * V) {
+            const int t = q >> 5, li = q & 31;
+            const int64_t g = gbase + li + t * gt;
+            cp_async16(&A[t * kLines + li], rho + g);
+            cp_async16(&B[t * kLines + li], a1 + g);
+        }
+    } else {
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            const int t = q >> 5, li = q & 31;
+            if (li < nl) {
+                const int64_t g = gbase + li + t * gt;
+                cp_async_elem(&A[t * kLines + li], rho + g);
+                cp_async_elem(&B[t * kLines + li], a1 + g);
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const int lane = threadIdx.x & 31, par = threadIdx.x >> 5;
+    const int m = (n - par + 1) / 2;
+    if (threadIdx.x < 2 * kLines && lane < nl) {
+        constexpr int kC = 8;
+        T z1 = 0, z2 = 0, up = 0;
+        for (int i0 = 0; i0 < m; i0 += kC) {
+            T r[kC], a[kC], uf[kC];
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int t = par + 2 * min(i0 + u, m - 1);
+                r[u] = A[t * kLines + lane];
+                a[u] = B[t * kLines + lane];
+                uf[u] = fs[t].y;
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (i0 + u < m) {
+                    const int k = (par + 2 * (i0 + u)) * kLines + lane;
+                    z1 = fma(-up, z1, fma(pq, a[u], r[u]));
+                    z2 = fma(-up, z2, a[u]);
+                    A[k] = z1;
+                    B[k] = z2;
+                    up = uf[u];
+                }
+        }
+        T x1 = 0, x2 = 0;
+        for (int i0 = m - 1; i0 >= 0; i0 -= kC) {
+            T za[kC + 1], zb[kC], ub[kC];
+            F2 ff[kC];
+#pragma unroll
+            for (int u = 0; u <= kC; ++u) {
+                const int i = max(i0 - u, 0);
+                za[u] = A[(par + 2 * i) * kLines + lane];
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int i = max(i0 - u, 0);
+                zb[u] = B[(par + 2 * i) * kLines + lane];
+                ff[u] = fs[par + 2 * i];
+                ub[u] = i >= 1 ? fs[par + 2 * i - 2].y : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kC; ++u)
+                if (i0 - u >= 0) {
+                    const int k = (par + 2 * (i0 - u)) * kLines + lane;
+                    x1 = fma(-ff[u].y, x1, ff[u].x * za[u]);
+                    x2 = fma(-ff[u].y, x2, ff[u].x * zb[u]);
+                    const T w = (i0 - u >= 1) ? fma(ub[u], za[u + 1], za[u]) : za[u];
+                    A[k] = fma(qp, x1, w);
+                    B[k] = x2;
+                }
+        }
+    }
+    __syncthreads();
+    // out: kU groups of V consecutive elements per thread, the old Z of all groups
+    // loaded before any store (as in cube_line_kernel)
+    const int vw = vec ? V : 1;
+    for (int q0 = threadIdx.x * vw; q0 < total; q0 += kU * blockDim.x * vw) {
+        T zo[kU][V];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int q = q0 + u * blockDim.x * vw;
+#pragma unroll
+            for (int w = 0; w < V; ++w) zo[u][w] = 0;
+            const int t = q >> 5, li = q & 31;
+            if (zacc != T(0) && q < total && (vec || li < nl)) {
+                const T *src = Z + gbase + li + t * gt;
+                if (vec) {
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 v4 = *reinterpret_cast<const float4 *>(src);
+                        zo[u][0] = v4.x, zo[u][1] = v4.y, zo[u][2] = v4.z, zo[u][3] = v4.w;
+                    } else {
+                        const double2 v2 = *reinterpret_cast<const double2 *>(src);
+                        zo[u][0] = v2.x, zo[u][1] = v2.y;
+                    }
+                } else {
+                    zo[u][0] = src[0];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int q = q0 + u * blockDim.x * vw;
+            const int t = q >> 5, li = q & 31;
+            if (q < total && (vec || li < nl)) {
+                const int k = t * kLines + li;
+                const int64_t g = gbase + li + t * gt;
+                if (vec) {
+                    T zr[V];
+#pragma unroll
+                    for (int w = 0; w < V; ++w) zr[w] = fma(qp, B[k + w], zacc * zo[u][w]);
+                    if constexpr (sizeof(T) == 4) {
+                        *reinterpret_cast<float4 *>(rho + g) = make_float4(A[k], A[k + 1], A[k + 2], A[k + 3]);
+                        *reinterpret_cast<float4 *>(Z + g) = make_float4(zr[0], zr[1], zr[2], zr[3]);
+                    } else {
+                        *reinterpret_cast<double2 *>(rho + g) = make_double2(A[k], A[k + 1]);
+                        *reinterpret_cast<double2 *>(Z + g) = make_double2(zr[0], zr[1]);
+                    }
+                } else {
+                    rho[g] = A[k];
+                    Z[g] = fma(qp, B[k], zacc * zo[u][0]);
+                }
+            }
+        }
+    }
+}
+
 // G = -F s_i s_j s_k (scale-in) or X = Y s_i s_j s_k (scale-out, sign = +1)
 __global__ void cube_scale_kernel(const double *__restrict__ A, double *__restrict__ B, const double *__restrict__ s,
                                   int n, double sign)
@@ -567,6 +723,8 @@ int CubeNested<T>::create(int64_t n, double tol, double tol_mid, double tol_in, 
                                  line_smem_bytes<T>((int)n, true, 2)));
     CUBE_CK(cudaFuncSetAttribute(cube_line_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  line_smem_bytes<T>((int)n, false, 2)));
+    CUBE_CK(cudaFuncSetAttribute(cube_dual_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 line_smem_bytes<T>((int)n, false, 2)));
     fac_entry_ = -1;
     slice_ = false;
     if (std::is_same<T, float>::value && residual_ && std::getenv("FPS_CUBE_SLICE") != nullptr)
@@ -746,9 +904,19 @@ int CubeNested<T>::stein_res(int ma, int mb, int entry, const T *R1, double r1, 
         const double p = S.p[l], q = S.q[l];
         if (l == 0) CUBE_CK(solve(1, R1, -r1, R2, -r2, a1, mb, 1.0, 0.0, 0.0, false));    // rho A~_b = R
         else CUBE_CK(solve(1 + 2 * l, rho, -1.0, nullptr, 0.0, a1, mb, 1.0, 0.0, 0.0, true));
-        if (l + 1 < S.J) CUBE_CK(solve(2 + 2 * l, rho, 1.0, a1, p - q, rho, ma, q - p, 0.0, 1.0, false));
-        CUBE_CK(solve(2 + 2 * l, a1, 1.0, nullptr, 0.0, Z, ma, q - p, (l > 0 || accumulate) ? 1.0 : 0.0, 0.0,
-                      false));
+        const double zacc = (l > 0 || accumulate) ? 1.0 : 0.0;
+        if (l + 1 < S.J) {  // both solves along ma in one launch
+            using F2 = typename V2<T>::type;
+            const int n = (int)n_;
+            const int nkb = (n + kLines - 1) / kLines;
+            cube_dual_kernel<T><<<n * nkb, kLineThreads, line_smem_bytes<T>(n, false, 2), st_>>>(
+                reinterpret_cast<const F2 *>(fac_) + (int64_t)(2 + 2 * l) * n, rho, a1, Z, n, ma, (T)(p - q),
+                (T)(q - p), (T)zacc);
+            ++launches;
+            CUBE_CK(cudaGetLastError());
+        } else {
+            CUBE_CK(solve(2 + 2 * l, a1, 1.0, nullptr, 0.0, Z, ma, q - p, zacc, 0.0, false));
+        }
     }
     return FPS_OK;
 }
