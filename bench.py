@@ -547,7 +547,8 @@ def main() -> None:
         },
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+            "frac": (achieved / hbm) if achieved else None,
+            "frac_survey": (achieved / hbm) if achieved else None, "traffic": traffic,
             "kernel": "ADI pass kernels (row pass + column pass of every inner iteration)",
             "bytes_per_launch": "12 B per element: the 6 FP32 words per element and iteration of the "
                                 "residual-form ADI (row pass: c, D read; D, result written; column pass: "
