@@ -484,11 +484,16 @@ __global__ void __launch_bounds__(kCT) col_pass_kernel(SwArgs<T> a, int j)
 //   W_s = wl_end(s) + phi_end(s) W_{s-1},           zin(s)  = W_{s-1}
 //   X_s = xl_start(s) + Bv_start(s) zin(s) + Psi_start(s) X_{s+1},   xout(s) = X_{s+1}
 // ---------------------------------------------------------------------------
-template <typename T>
+// BIG: long load batches (fewer dependent round trips to L2, more registers) for
+// grids of a few CTAs per SM, where latency is all; short ones keep occupancy when
+// the grid fills the GPU (batches of many problems).
+template <typename T, bool BIG>
 __global__ void __launch_bounds__(2 * kChainLines) chain_kernel(SwArgs<T> a, int dir, int j)
 {
     using T2 = typename Vec2<T>::type;
-    constexpr int B = 16;  // segments whose loads are issued together
+    // segments whose loads are issued together (forward: 2 values, backward: 4 values
+    // per segment); each batch is one dependent round trip to L2
+    constexpr int B = BIG ? (sizeof(T) == 4 ? 40 : 20) : 16, B2 = BIG ? (sizeof(T) == 4 ? 24 : 12) : 16;
     const int4 it = a.items[blockIdx.x];
     const SwProb<T> &pr = a.probs[it.x];
     if (!a.active[it.x] || j >= pr.J) return;
@@ -523,10 +528,10 @@ __global__ void __launch_bounds__(2 * kChainLines) chain_kernel(SwArgs<T> a, int
         }
     }
     T X = 0;
-    for (int s1 = P - 1; s1 >= 0; s1 -= B) {
-        T sy[B], zi[B], bv[B], ps[B];
+    for (int s1 = P - 1; s1 >= 0; s1 -= B2) {
+        T sy[B2], zi[B2], bv[B2], ps[B2];
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
+        for (int b = 0; b < B2; ++b) {
             const int s = s1 - b;
             if (s >= 0) {
                 sy[b] = sum[s * step].y;
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(2 * kChainLines) chain_kernel(SwArgs<T> a, int
             }
         }
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
+        for (int b = 0; b < B2; ++b) {
             const int s = s1 - b;
             if (s >= 0) {
                 zx[s * step] = mk2<T>(zi[b], X);
@@ -857,7 +862,10 @@ cudaError_t launch_col_pass(const SwArgs<T> &a, int j, cudaStream_t st)
 template <typename T>
 cudaError_t launch_chain(const SwArgs<T> &a, int dir, int j, cudaStream_t st)
 {
-    chain_kernel<T><<<(unsigned)a.nitems, 2 * kChainLines, 0, st>>>(a, dir, j);
+    if (a.nitems <= 2 * (int64_t)current_sm_count())
+        chain_kernel<T, true><<<(unsigned)a.nitems, 2 * kChainLines, 0, st>>>(a, dir, j);
+    else
+        chain_kernel<T, false><<<(unsigned)a.nitems, 2 * kChainLines, 0, st>>>(a, dir, j);
     return cudaGetLastError();
 }
 
