@@ -715,6 +715,9 @@ __global__ void __launch_bounds__(256) residual_kernel(TileArgs t, const double 
                                                        const int *__restrict__ pair_active, int y_zero)
 {
     __shared__ double Ys[36][37];
+    // stencil coefficients of the tile's rows and columns: -kx d_i, -kx e_{i-2}, -kx e_i
+    // and -ky d_k, -ky e_{k-2}, -ky e_k (formed once per tile, not per element)
+    __shared__ double cr[3][32], cc[3][32];
     int64_t t0, t1;
     tile_run(t.ntiles, t0, t1);
     double local = 0.0;
@@ -749,17 +752,34 @@ __global__ void __launch_bounds__(256) residual_kernel(TileArgs t, const double 
                 Ys[r][cc] = val;
             }
         }
+        {
+            const int q = ty * 32 + tx;  // 192 of the 256 threads form one coefficient each
+            if (q < 192) {
+                const int which = q >> 5, w = q & 31, set = which % 3;
+                const bool row = which < 3;
+                const int idx = (row ? v.by : v.bx) + w;
+                const double sc = row ? v.kx : v.ky;
+                double c = 0.0;
+                if (idx < n) {
+                    if (set == 0) c = -sc * v.d[idx];
+                    else if (set == 1) c = idx >= 2 ? -sc * v.e[idx - 2] : 0.0;
+                    else c = -sc * v.e[idx];  // e[idx] = 0 when idx + 2 >= n
+                }
+                (row ? cr : cc)[set][w] = c;
+            }
+        }
         __syncthreads();
         for (int r = ty; r < 32; r += 8) {
             const int i = v.by + r, k = v.bx + tx;
             if (i < n && k < n) {
                 const double y = Ys[r + 2][tx + 2];
                 double acc = Ft[v.off64 + (int64_t)i * n + k];
-                acc = fma(-(v.kx * v.d[i] + v.ky * v.d[k]), y, acc);
-                if (i >= 2) acc = fma(-v.kx * v.e[i - 2], Ys[r][tx + 2], acc);
-                acc = fma(-v.kx * v.e[i], Ys[r + 4][tx + 2], acc);  // e[i] = 0 when i + 2 >= n
-                if (k >= 2) acc = fma(-v.ky * v.e[k - 2], Ys[r + 2][tx], acc);
-                acc = fma(-v.ky * v.e[k], Ys[r + 2][tx + 4], acc);
+                // halo entries outside [0, n) are zero in Ys, and so are their coefficients
+                acc = fma(cr[0][r] + cc[0][tx], y, acc);
+                acc = fma(cr[1][r], Ys[r][tx + 2], acc);
+                acc = fma(cr[2][r], Ys[r + 4][tx + 2], acc);
+                acc = fma(cc[1][tx], Ys[r + 2][tx], acc);
+                acc = fma(cc[2][tx], Ys[r + 2][tx + 4], acc);
                 Yout[v.off64 + (int64_t)i * n + k] = y;
                 local = flag_nonfinite(fabs(acc), local);
                 rho0[v.offT + (int64_t)(i + 2) * v.ldp + k + 4] = (float)(acc * inv);
