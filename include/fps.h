@@ -85,6 +85,9 @@ typedef struct {
                                by the autotuner unless FPS_AUTOTUNE=0 */
     int64_t inner_iterations; /* cube: inner (slice Stein) ADI iterations over full
                                  tensors in the last solve, all levels and rounds */
+    int chain_mode;         /* square plans: load batching of the segment-coupling kernel
+                               (1 short, 2 long batches; FP32_REFINE: picked by the autotuner
+                               with seg_len, 0 = chosen by grid size when it did not run) */
 } fps_plan_info_t;
 
 /*

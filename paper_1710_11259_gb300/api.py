@@ -57,6 +57,7 @@ class PlanInfo(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64),
         ("seg_len", ctypes.c_int),
         ("inner_iterations", ctypes.c_int64),
+        ("chain_mode", ctypes.c_int),
     ]
 
 

@@ -685,6 +685,7 @@ int fps_plan_info(const fps_plan *plan, fps_plan_info_t *info)
     info->device_bytes = plan->bytes;
     info->kernel_launches = plan->launches_last;
     info->seg_len = plan->eng32 ? plan->eng32->seg_len : (plan->eng64 ? plan->eng64->seg_len : 0);
+    info->chain_mode = plan->eng32 ? plan->eng32->chain_mode : (plan->eng64 ? plan->eng64->chain_mode : 0);
     return FPS_OK;
 }
 

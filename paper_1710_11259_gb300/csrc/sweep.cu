@@ -882,7 +882,8 @@ cudaError_t launch_col_pass(const SwArgs<T> &a, int j, cudaStream_t st)
 template <typename T>
 cudaError_t launch_chain(const SwArgs<T> &a, int dir, int j, cudaStream_t st)
 {
-    if (a.nitems <= 2 * (int64_t)current_sm_count())
+    const bool big = a.chain_mode == 2 || (a.chain_mode == 0 && a.nitems <= 2 * (int64_t)current_sm_count());
+    if (big)
         chain_kernel<T, true><<<(unsigned)a.nitems, 2 * kChainLines, 0, st>>>(a, dir, j);
     else
         chain_kernel<T, false><<<(unsigned)a.nitems, 2 * kChainLines, 0, st>>>(a, dir, j);

@@ -94,6 +94,7 @@ struct SwArgs {
     T *zin;                // chain scratch ([P][2][N + 8] per rhs)
     int *err;              // device error word: bit 0 = a bounded wait gave up
     int S;                 // segment length of every problem (sweep_segment_supported)
+    int chain_mode;        // chain kernel loads: 0 = by grid size, 1 = short batches, 2 = long batches
 };
 
 // Elementwise tile kernels of the solve around the ADI loop.  A tile item is

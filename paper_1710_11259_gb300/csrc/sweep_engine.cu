@@ -141,6 +141,29 @@ int SweepEngine<T>::time_level(size_t li, int reps, float &ms, std::string &err)
     return FPS_OK;
 }
 
+// Mean time of a chain launch (both directions alternately) with the given load
+// batching, on this engine's arrays (the values do not change the time).
+template <typename T>
+int SweepEngine<T>::time_chain(int mode, float &ms, std::string &err)
+{
+    SwArgs<T> a = args(levels_.back(), 2);
+    a.chain_mode = mode;
+    cudaEvent_t e0, e1;
+    ENG_CK(cudaEventCreate(&e0));
+    ENG_CK(cudaEventCreate(&e1));
+    ENG_CK(launch_chain(a, 0, 0, cap_));  // warm-up
+    ENG_CK(cudaEventRecord(e0, cap_));
+    constexpr int kReps = 20;
+    for (int r = 0; r < kReps; ++r) ENG_CK(launch_chain(a, r & 1, 0, cap_));
+    ENG_CK(cudaEventRecord(e1, cap_));
+    ENG_CK(cudaEventSynchronize(e1));
+    ENG_CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ms /= (float)kReps;
+    return FPS_OK;
+}
+
 template <typename T>
 int SweepEngine<T>::autotune(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight, std::string &err)
 {
@@ -151,14 +174,22 @@ int SweepEngine<T>::autotune(const std::vector<int64_t> &ns, int nrhs, double to
     const std::string path = tune_cache_path();
     {
         std::ifstream in(path);
-        std::string k;
-        int v;
-        while (in >> k >> v)
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string k;
+            int v = 0, cm = 0;
+            if (!(ls >> k >> v)) continue;
+            if (!(ls >> cm) || cm < 0 || cm > 2) cm = 0;  // entries without a chain mode: by grid size
             if (k == key && sweep_segment_supported(false, v)) {
                 seg_len = v;
+                chain_mode = cm;
                 return FPS_OK;
             }
+        }
     }
+    // tile shape: the segment length of the passes (a whole graph level timed per
+    // candidate); then the chain kernel's load batching, timed on the winner's arrays
     const int cand[] = {64, 128};
     float best = 3.4e38f;
     tune_ms.clear();
@@ -166,8 +197,10 @@ int SweepEngine<T>::autotune(const std::vector<int64_t> &ns, int nrhs, double to
         SweepEngine<T> t;
         std::string e2;
         int st = t.create(ns, nrhs, tol, tight, cap_, e2, S, kx_, ky_);
-        float ms = 0.f;
+        float ms = 0.f, c1 = 0.f, c2 = 0.f;
         if (st == FPS_OK) st = t.time_level(t.levels_.size() - 1, 2, ms, e2);
+        if (st == FPS_OK) st = t.time_chain(1, c1, e2);
+        if (st == FPS_OK) st = t.time_chain(2, c2, e2);
         t.release();
         if (st != FPS_OK) {
             err = "autotune: " + e2;
@@ -177,12 +210,13 @@ int SweepEngine<T>::autotune(const std::vector<int64_t> &ns, int nrhs, double to
         if (ms < best) {
             best = ms;
             seg_len = S;
+            chain_mode = c2 < c1 ? 2 : 1;
         }
     }
     const size_t slash = path.find_last_of('/');
     if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // may exist
     std::ofstream out(path, std::ios::app);
-    if (out) out << key << " " << seg_len << "\n";
+    if (out) out << key << " " << seg_len << " " << chain_mode << "\n";
     return FPS_OK;
 }
 
@@ -502,6 +536,7 @@ SwArgs<T> SweepEngine<T>::args(const Level &L, int which) const
     a.zin = zin_;
     a.err = err_;
     a.S = seg_len;
+    a.chain_mode = chain_mode;
     return a;
 }
 

@@ -47,6 +47,7 @@ public:
     int max_rounds = 8;
     std::vector<std::vector<double>> shifts;  // level-0 shifts per problem
     int seg_len = 0;                          // segment length in use
+    int chain_mode = 0;                       // chain kernel load batching (SwArgs::chain_mode)
     std::vector<float> tune_ms;               // autotuner timings per candidate (ms), if it ran
     int64_t total_elems() const { return tot64_; }
 
@@ -65,6 +66,7 @@ private:
     int build_graph(Level &L, std::string &err);
     int autotune(const std::vector<int64_t> &ns, int nrhs, double tol, bool tight, std::string &err);
     int time_level(size_t li, int reps, float &ms, std::string &err);
+    int time_chain(int mode, float &ms, std::string &err);
     SwArgs<T> args(const Level &L, int which) const;
     int solve_refine(const double *F, double *X, cudaStream_t st, std::string &err);
     int solve_plain(const double *F, double *X, cudaStream_t st, std::string &err);

@@ -110,12 +110,14 @@ def test_autotuner_picks_and_caches(api, tmp_path, monkeypatch):
     ns = [300, 257, 64, 33]
     plan = api.plan_create_batched(ns, nrhs=2, tol=1e-10, precision="fp32_refine")
     chosen = api.plan_info(plan)["seg_len"]
+    chosen_chain = api.plan_info(plan)["chain_mode"]
     api.plan_destroy(plan)
-    assert chosen in {64, 128}
+    assert chosen in {64, 128} and chosen_chain in {1, 2}
+    assert cache.read_text().split()[1:3] == [str(chosen), str(chosen_chain)]
     lines = cache.read_text().split("\n")
     assert len([ln for ln in lines if ln.strip()]) == 1
     plan = api.plan_create_batched(ns, nrhs=2, tol=1e-10, precision="fp32_refine")
-    assert api.plan_info(plan)["seg_len"] == chosen
+    assert api.plan_info(plan)["seg_len"] == chosen and api.plan_info(plan)["chain_mode"] == chosen_chain
     F = torch.from_numpy(np.concatenate([inputs.square_rhs(n, 60 + n).ravel() for n in ns for _ in range(2)])).cuda()
     X = api.poisson_square_solve(plan, F)
     torch.cuda.synchronize()
@@ -131,10 +133,10 @@ def test_autotuner_picks_and_caches(api, tmp_path, monkeypatch):
             o += n * n
 
 
-@pytest.mark.parametrize("seg", ["64", "128"])
-def test_both_segment_lengths_match_oracle(api, tmp_path, monkeypatch, seg):
-    """Each compiled segment length, forced through the cache, on sizes with a short
-    last segment (n = 200, 321) and a single segment (n = 33)."""
+@pytest.mark.parametrize("seg,chain", [("64", 1), ("64", 2), ("128", 1), ("128", 2)])
+def test_both_segment_lengths_match_oracle(api, tmp_path, monkeypatch, seg, chain):
+    """Each compiled segment length and chain-kernel load batching, forced through the
+    cache, on sizes with a short last segment (n = 200, 321) and a single segment (n = 33)."""
     ns = [321, 200, 33]
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("FPS_AUTOTUNE_CACHE", str(cache))
@@ -142,9 +144,9 @@ def test_both_segment_lengths_match_oracle(api, tmp_path, monkeypatch, seg):
     plan = api.plan_create_batched(ns, nrhs=1, tol=1e-10, precision="fp32_refine")
     key = cache.read_text().split()[0]
     api.plan_destroy(plan)
-    cache.write_text(f"{key} {seg}\n")
+    cache.write_text(f"{key} {seg} {chain}\n")
     plan = api.plan_create_batched(ns, nrhs=1, tol=1e-10, precision="fp32_refine")
-    assert api.plan_info(plan)["seg_len"] == int(seg)
+    assert api.plan_info(plan)["seg_len"] == int(seg) and api.plan_info(plan)["chain_mode"] == chain
     rng = np.random.default_rng(77)
     rhs = [rng.standard_normal((1, n, n)) * inputs.decay_weights(n, 2)[None, :, None] *
            inputs.decay_weights(n, 2)[None, None, :] for n in ns]
