@@ -105,8 +105,9 @@ typedef struct {
  * Every shift list is validated on the host before any kernel runs (finite, inside
  * the spectral interval).  Environment: FPS_MAX_REFINE_ROUNDS caps the refinement
  * rounds of FP32_REFINE plans (default 8 for squares, 12 for cubes);
- * FPS_CUBE_STREAMING=1 makes FP32 cube plans run their inner level by whole-tensor
- * line solves instead of the slice-resident cluster kernel; FPS_INJECT_SHIFT_FAULT=nan|neg corrupts
+ * FPS_CUBE_SLICE=1 makes FP32 cube plans (n <= 256) run their inner level with the
+ * slice-resident cluster kernel instead of the default whole-tensor line solves
+ * (measured slower; kept as an option); FPS_INJECT_SHIFT_FAULT=nan|neg corrupts
  * the first shift before validation (host-side fault injection for tests).
  * Errors: INVALID_ARG (n < 1, dim not 2/3, tol outside (0,1), nrhs < 1, out NULL, a
  * shift list that fails validation), CUDA (allocation or launch failure).  *out is
