@@ -25,6 +25,9 @@
  *   - The caller owns F, X and gradient buffers; the plan owns everything else
  *     (shift table, per-shift Thomas factors, work arrays, CUDA graph).
  *   - F is never modified.  X must not overlap F.
+ *   - Device buffers must be memory of the plan's device (of the current device for
+ *     the plan-free calls) or managed memory; device memory of another device is
+ *     rejected with INVALID_ARG.
  *   - Errors from argument checks are returned synchronously; errors from the
  *     device (a failed launch) are returned by the call that detects them.
  *     fps_last_error() gives a one-line message for the calling thread.
@@ -148,8 +151,8 @@ int fps_plan_set_stream(fps_plan *plan, void *stream);
  * fps_poisson_square_solve -- X = solution of (3.6) for F (per right-hand side,
  * per problem of a batch).  Algorithm 2 on A~ Y + Y A~ = F~ of (3.9), then
  * X = D_s Y D_s (the recovery consistent with the printed right-hand side of (3.9)).
- * Errors: INVALID_ARG (plan NULL or not dim 2, F/X NULL or overlapping),
- * NONFINITE (FP32_REFINE: F holds NaN/Inf), NOT_CONVERGED (FP32_REFINE missed tol),
+ * Errors: INVALID_ARG (plan NULL or not dim 2, F/X NULL or overlapping, F/X device
+ * memory of another device), NONFINITE (FP32_REFINE: F holds NaN/Inf), NOT_CONVERGED (FP32_REFINE missed tol),
  * CUDA.
  */
 int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X);
@@ -169,7 +172,8 @@ int fps_poisson_square_solve(fps_plan *plan, const double *F, double *X);
  * R = G - (T_01 + T_02 + T_12) Y of the symmetrised equation (G = -F/sqrt(E_i E_j E_k))
  * until max |R| / max |G| <= tol (at most 12 rounds).  Plans: dim = 3, n <= 320.
  * X[(i*n + j)*n + k] pairs C~_i(x) C~_j(y) C~_k(z).  Host or device F and X.
- * Errors: INVALID_ARG (plan not dim 3, NULL/overlapping buffers), UNSUPPORTED
+ * Errors: INVALID_ARG (plan not dim 3, NULL/overlapping buffers, device memory of
+ * another device), UNSUPPORTED
  * (n > 320 at plan creation), NONFINITE (FP32_REFINE: F holds NaN/Inf),
  * NOT_CONVERGED (FP32_REFINE missed tol; X holds the last iterate), CUDA.
  */
@@ -233,7 +237,7 @@ int fps_plan_pass_times(fps_plan *plan, double *row_ms, double *col_ms);
  * banded: F = B G B^T, B[j][j] = 1/((2j+1) s_j), B[j][j+2] = -1/((2j+5) s_j),
  * C~_k = s_k C^(3/2)_k.  G and F: device pointers, n x n row-major, caller-owned,
  * not overlapping; asynchronous on `stream`.  Errors: INVALID_ARG (n < 1, NULL,
- * overlap, host memory), CUDA.
+ * overlap, host memory or memory of a device other than the current one), CUDA.
  */
 int fps_legendre_to_ctilde(int64_t n, const double *G, double *F, void *stream);
 
@@ -245,7 +249,7 @@ int fps_legendre_to_ctilde(int64_t n, const double *G, double *F, void *stream);
  * L[j][j] = c_j, L[j+2][j] = -c_j, c_j = s_j (j+1)(j+2)/(2j+3).  X (n x n) and U
  * ((n+2) x (n+2)): device pointers, row-major, caller-owned, not overlapping;
  * asynchronous on `stream`.  Errors: INVALID_ARG (n < 1, NULL, overlap, host
- * memory), CUDA.
+ * memory or memory of a device other than the current one), CUDA.
  */
 int fps_solution_to_legendre(int64_t n, const double *X, double *U, void *stream);
 
@@ -308,7 +312,8 @@ int fps_plan_create_cylinder(fps_plan **out, int64_t n, int64_t kmin, int64_t km
  * fps_poisson_cylinder_solve -- Y for every (mode, right-hand side) of a cylinder plan.
  * F, Y: device pointers of the plan's device, [kmax - kmin + 1][nrhs][n][n] row-major,
  * caller-owned, not overlapping; asynchronous on the plan's stream.  Errors:
- * INVALID_ARG (not a cylinder plan, NULL, overlap, host memory), CUDA.
+ * INVALID_ARG (not a cylinder plan, NULL, overlap, host memory or memory of another
+ * device), CUDA.
  */
 int fps_poisson_cylinder_solve(fps_plan *plan, const double *F, double *Y);
 

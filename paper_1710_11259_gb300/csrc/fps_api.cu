@@ -52,15 +52,33 @@ struct DeviceGuard {
     }
 };
 
-bool is_device_pointer(const void *p)
+// Where a caller's buffer lives, seen from the device `dev` whose kernels will touch it:
+// device memory of `dev` or managed memory (kDevice), pageable or pinned host memory
+// (kHost, staged through device scratch where an entry point accepts it), or device memory
+// of another device (kForeign: rejected everywhere, since the kernels would make peer
+// accesses that may not even be enabled).
+enum class Mem { kHost, kDevice, kForeign };
+
+Mem memory_kind(const void *p, int dev)
 {
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return Mem::kHost;
     }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    if (attr.type == cudaMemoryTypeManaged) return Mem::kDevice;
+    if (attr.type == cudaMemoryTypeDevice) return attr.device == dev ? Mem::kDevice : Mem::kForeign;
+    return Mem::kHost;
 }
+
+int current_device()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    return dev;
+}
+
+bool is_device_pointer(const void *p, int dev) { return memory_kind(p, dev) == Mem::kDevice; }
 
 }  // namespace
 
@@ -216,7 +234,10 @@ int solve_square(fps_plan *p, const double *F, double *X, const char *what)
     const char *f0 = (const char *)F, *x0 = (const char *)X;
     if (f0 < x0 + bytes && x0 < f0 + bytes) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and X overlap");
     DeviceGuard g(p->device);
-    const bool fdev = is_device_pointer(F), xdev = is_device_pointer(X);
+    const Mem fk = memory_kind(F, p->device), xk = memory_kind(X, p->device);
+    if (fk == Mem::kForeign || xk == Mem::kForeign)
+        return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F or X is device memory of another device");
+    const bool fdev = fk == Mem::kDevice, xdev = xk == Mem::kDevice;
     p->launches_last = 0;
     if (p->small) return solve_small(p, F, X, fdev, xdev, what);
     if (p->eng32) return solve_engine(p, p->eng32, F, X, fdev, xdev, what);
@@ -327,9 +348,11 @@ int dirichlet_check(fps_plan *p, std::initializer_list<const void *> ptrs, const
         return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": needs a single square or rectangle plan");
     for (const void *q : ptrs) {
         if (!q) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": NULL buffer");
-        if (!is_device_pointer(q)) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": buffers must be device memory");
+        if (!is_device_pointer(q, p->device))
+            return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": buffers must be device memory of the plan's device");
     }
     if (!p->dir_F) {
+        DeviceGuard g(p->device);
         const size_t nn = (size_t)p->total_elems;
         FPS_CK(cudaMalloc((void **)&p->dir_F, sizeof(double) * nn));
         FPS_CK(cudaMalloc((void **)&p->dir_X, sizeof(double) * nn));
@@ -484,7 +507,10 @@ int fps_poisson_cube_solve(fps_plan *plan, const double *F, double *X)
     const char *f0 = (const char *)F, *x0 = (const char *)X;
     if (f0 < x0 + bytes && x0 < f0 + bytes) return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: F and X overlap");
     DeviceGuard g(plan->device);
-    const bool fdev = is_device_pointer(F), xdev = is_device_pointer(X);
+    const Mem fk = memory_kind(F, plan->device), xk = memory_kind(X, plan->device);
+    if (fk == Mem::kForeign || xk == Mem::kForeign)
+        return fail(FPS_ERR_INVALID_ARG, "fps_poisson_cube_solve: F or X is device memory of another device");
+    const bool fdev = fk == Mem::kDevice, xdev = xk == Mem::kDevice;
     if ((!fdev || !xdev) && !plan->stage_in) {
         FPS_CK(cudaMalloc((void **)&plan->stage_in, sizeof(double) * n3));
         FPS_CK(cudaMalloc((void **)&plan->stage_out, sizeof(double) * n3));
@@ -623,8 +649,8 @@ int fps_poisson_cylinder_solve(fps_plan *plan, const double *F, double *Y)
     const size_t bytes = sizeof(double) * (size_t)plan->total_elems;
     const char *f0 = (const char *)F, *y0 = (const char *)Y;
     if (f0 < y0 + bytes && y0 < f0 + bytes) return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and Y overlap");
-    if (!is_device_pointer(F) || !is_device_pointer(Y))
-        return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and Y must be device memory");
+    if (!is_device_pointer(F, plan->device) || !is_device_pointer(Y, plan->device))
+        return fail(FPS_ERR_INVALID_ARG, std::string(what) + ": F and Y must be device memory of the plan's device");
     DeviceGuard g(plan->device);
     std::string err;
     const int st = plan->cyl->solve(F, Y, plan->stream, err);
@@ -825,8 +851,9 @@ int fps_legendre_to_ctilde(int64_t n, const double *G, double *F, void *stream)
     const size_t bytes = sizeof(double) * (size_t)n * (size_t)n;
     const char *g0 = (const char *)G, *f0 = (const char *)F;
     if (g0 < f0 + bytes && f0 < g0 + bytes) return fail(FPS_ERR_INVALID_ARG, "fps_legendre_to_ctilde: G and F overlap");
-    if (!is_device_pointer(G) || !is_device_pointer(F))
-        return fail(FPS_ERR_INVALID_ARG, "fps_legendre_to_ctilde: G and F must be device memory");
+    const int dev = current_device();
+    if (!is_device_pointer(G, dev) || !is_device_pointer(F, dev))
+        return fail(FPS_ERR_INVALID_ARG, "fps_legendre_to_ctilde: G and F must be device memory of the current device");
     FPS_CK(fps::launch_legendre_to_ctilde(G, F, n, (cudaStream_t)stream));
     return FPS_OK;
 }
@@ -839,8 +866,9 @@ int fps_solution_to_legendre(int64_t n, const double *X, double *U, void *stream
     const size_t ub = sizeof(double) * (size_t)(n + 2) * (size_t)(n + 2);
     const char *x0 = (const char *)X, *u0 = (const char *)U;
     if (x0 < u0 + ub && u0 < x0 + xb) return fail(FPS_ERR_INVALID_ARG, "fps_solution_to_legendre: X and U overlap");
-    if (!is_device_pointer(X) || !is_device_pointer(U))
-        return fail(FPS_ERR_INVALID_ARG, "fps_solution_to_legendre: X and U must be device memory");
+    const int dev = current_device();
+    if (!is_device_pointer(X, dev) || !is_device_pointer(U, dev))
+        return fail(FPS_ERR_INVALID_ARG, "fps_solution_to_legendre: X and U must be device memory of the current device");
     FPS_CK(fps::launch_solution_to_legendre(X, U, n, (cudaStream_t)stream));
     return FPS_OK;
 }
