@@ -864,10 +864,11 @@ int CubeNested<T>::hsolve(const Outer &o, const T *R, T *Y, std::string &err)
 // rho = C - A Z + Z B the two half-steps of Algorithm 2 become
 //   rho+ = (A - q)^{-1} (A - p) rho (B - p)^{-1} (B - q),
 //   Z+   = Z + (q - p) (A - q)^{-1} rho (B - p)^{-1},
-// and rho (B - p)^{-1} = -rho A~_b (c + p A~_b)^{-1}.  Per iteration three line-solve
-// launches: a1 = rho (B - p)^{-1} along b (the product with A~_b folded in), then
-// along a rho+ = c1 + (q - p)(A - q)^{-1} c1 with c1 = rho + (p - q) a1 (in place)
-// and Z += (q - p)(A - q)^{-1} a1.  Solves Z = (T_ab + c)^{-1} (r1 R1 + r2 R2), or
+// and rho (B - p)^{-1} = -rho A~_b (c + p A~_b)^{-1}.  Per iteration two launches:
+// a1 = rho (B - p)^{-1} along b (the product with A~_b folded in), then one
+// cube_dual_kernel along a for rho+ = c1 + (q - p)(A - q)^{-1} c1 with
+// c1 = rho + (p - q) a1 (in place) and Z += (q - p)(A - q)^{-1} a1 (the last
+// iteration needs only the Z solve).  Solves Z = (T_ab + c)^{-1} (r1 R1 + r2 R2), or
 // adds it to Z when accumulate.  Uses work_[0], work_[1].
 template <typename T>
 int CubeNested<T>::stein_res(int ma, int mb, int entry, const T *R1, double r1, const T *R2, double r2, T *Z,
