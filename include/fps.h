@@ -301,9 +301,11 @@ int fps_poisson_dirichlet_adjoint(fps_plan *plan, const double *dLdU, double *dL
  * B = -M D^{-1}, multiplied through by P so that only banded solves and products
  * remain; shifts (2.4) per mode from an interval of sigma(A_k) found by power
  * iteration (widened by 3 %) and the tight interval of sigma(B); J of (2.9) per mode.
- * FP64.  n in [4, 4096], nrhs right-hand sides per mode (e.g. the real and imaginary
- * parts of f_k and f_{-k}).  Errors: INVALID_ARG, UNSUPPORTED (an interval or a pivot
- * that cannot be formed), CUDA.
+ * FP64.  n >= 4, nrhs right-hand sides per mode (e.g. the real and imaginary parts
+ * of f_k and f_{-k}).  The line kernels hold 32 whole lines per CTA in shared memory
+ * (about 352 n bytes), so n is bounded by the device's per-CTA limit: n <= 660 on
+ * GB300 (227 KB).  Errors: INVALID_ARG, UNSUPPORTED (n above that bound or above
+ * 4096, an interval or a pivot that cannot be formed), CUDA.
  */
 int fps_plan_create_cylinder(fps_plan **out, int64_t n, int64_t kmin, int64_t kmax, double tol, int nrhs,
                              void *stream);

@@ -514,6 +514,17 @@ int CylinderEngine::create(int64_t n_, int64_t kmin_, int64_t kmax_, double tol,
     kmax = kmax_;
     nrhs = nrhs_;
     const int modes = (int)(kmax - kmin + 1);
+    // Both kernels hold whole lines of 32 (mode, rhs) rows or columns in shared
+    // memory: about 352 n bytes per CTA, n <= 660 at 227 KB.
+    int dev = 0, optin = 0;
+    CYL_CK(cudaGetDevice(&dev));
+    CYL_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int need = std::max(z_smem((int)n), r_smem((int)n));
+    if (need > optin) {
+        err = "n = " + std::to_string(n) + " needs " + std::to_string(need) +
+              " bytes of shared memory per CTA (device limit " + std::to_string(optin) + ")";
+        return FPS_ERR_UNSUPPORTED;
+    }
     // sigma(B) = sigma(-M D^{-1}) = sigma(-A~): the tight interval of A~
     lo = square_eps(n);
     hi = 1.0;

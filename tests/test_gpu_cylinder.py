@@ -132,3 +132,13 @@ def test_cylinder_rejects_host_buffers(api):
         api.poisson_cylinder_solve(plan, F, np.empty_like(F))
     api.plan_destroy(plan)
     assert e.value.status == -1
+
+
+def test_cylinder_rejects_n_beyond_shared_memory(api):
+    """The line kernels keep 32 whole lines per CTA on chip (about 352 n bytes): at
+    n = 4096 that is 1.4 MB, above any device's per-CTA limit, and plan creation
+    refuses it with UNSUPPORTED before allocating anything."""
+    with pytest.raises(api.FpsError) as e:
+        api.plan_create_cylinder(4096, 2, 2, 1e-12, 1)
+    assert e.value.status == -2
+    assert "shared memory" in str(e.value)
