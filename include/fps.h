@@ -322,7 +322,7 @@ int fps_poisson_cylinder_solve(fps_plan *plan, const double *F, double *Y);
 /*
  * fps_cylinder_mode_interval -- host helper: the interval [*a, *b] (a < b < 0) the
  * cylinder plan uses for sigma(A_k), A_k = P^{-1} Q of size n.  Errors: INVALID_ARG
- * (n < 4, k < 2, NULL), UNSUPPORTED.
+ * (n outside [4, 4096], k < 2, NULL), UNSUPPORTED.
  */
 int fps_cylinder_mode_interval(int64_t n, int64_t k, double *a, double *b);
 

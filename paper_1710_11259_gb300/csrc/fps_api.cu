@@ -661,7 +661,8 @@ int fps_poisson_cylinder_solve(fps_plan *plan, const double *F, double *Y)
 
 int fps_cylinder_mode_interval(int64_t n, int64_t k, double *a, double *b)
 {
-    if (n < 4 || k < 2 || !a || !b) return fail(FPS_ERR_INVALID_ARG, "fps_cylinder_mode_interval: need n >= 4, k >= 2");
+    if (n < 4 || n > 4096 || k < 2 || !a || !b)
+        return fail(FPS_ERR_INVALID_ARG, "fps_cylinder_mode_interval: need 4 <= n <= 4096, k >= 2");
     if (fps::cyl_mode_interval(n, k, *a, *b) != FPS_OK)
         return fail(FPS_ERR_UNSUPPORTED, "fps_cylinder_mode_interval: power iteration failed");
     return FPS_OK;

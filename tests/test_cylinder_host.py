@@ -46,3 +46,7 @@ def test_cylinder_argument_errors(L):
     assert L.fps_poisson_cylinder_solve(None, None, None) == -1
     with pytest.raises(api.FpsError):
         api.cylinder_mode_interval(16, 1)
+    with pytest.raises(api.FpsError):
+        api.cylinder_mode_interval(4097, 2)
+    with pytest.raises(api.FpsError):
+        api.cylinder_operators(4097)
